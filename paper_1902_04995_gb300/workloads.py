@@ -1,0 +1,232 @@
+"""Seeded synthetic LP batches (the only module shared by the CUDA path's callers
+and the oracle's tests).
+
+It holds none of the solver's arithmetic: it draws random constraint sets with
+numpy's PCG64 (``default_rng``) and lays them out as the library expects:
+
+* ``ax, ay, b``  float32 [n_constraints]   constraint i is  ax[i]*x + ay[i]*y <= b[i]
+* ``offsets``    int64  [n_lp + 1]         LP l owns constraints offsets[l] .. offsets[l+1]-1
+* ``obj``        float32 [n_lp, 2]         objective (c_x, c_y) per LP, maximised
+* ``box``        (xmin, xmax, ymin, ymax)  the bounding constraints (+-M, Sec. 2.1)
+
+The paper generates random feasible 2-D constraint sets (Sec. 4); these generators
+stand in for that, with distinct LPs instead of one LP copied across the batch.
+
+"Disk" family (the plain, at-scale and ragged workloads):
+  per LP a centre c ~ U[-1,1]^2; per constraint a unit normal n at angle ~ U[0, 2pi),
+  r ~ U[0.5, 2] and b = r + n.c, so c is strictly feasible (margin >= 0.5) and every
+  LP is feasible; the objective is a unit vector at angle ~ U[0, 2pi).
+  A fraction of LPs is made infeasible by appending one constraint  -u.x <= -(H + 1),
+  where H >= max over the feasible polygon of u.x.  H comes from weak duality: u is
+  written as alpha*n_i + beta*n_j (alpha, beta >= 0) with n_i, n_j the stored normals
+  that bracket u in angle, so u.x <= alpha*b_i + beta*b_j for every feasible x.
+  Directions whose bracketing gap is >= pi (polygon unbounded there) are redrawn.
+
+Collision-avoidance family (the precision workload):
+  a 16-gon of inradius R ~ U[1, 2] around the origin (normals at 2*pi*k/16) plus
+  K ~ U{10..100} neighbour half-planes with normal p/|p|, p ~ U[-5,5]^2 and offset
+  ~ U[0, 0.5]; 5 % of neighbour normals are replaced by a copy of an earlier normal
+  of the same LP rotated by delta ~ U(-1e-6, 1e-6) rad (near-parallel pairs).  The
+  origin is feasible in every LP; the objective is a unit preferred-velocity direction.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+DEFAULT_SEED = 20190213
+BOX_M = 1e3
+DEFAULT_BOX = (-BOX_M, BOX_M, -BOX_M, BOX_M)
+
+
+def _disk_constraints(rng, sizes):
+    """Constraints of the disk family for LPs of the given sizes (float32 SoA)."""
+    n_lp = sizes.shape[0]
+    offsets = np.zeros(n_lp + 1, dtype=np.int64)
+    np.cumsum(sizes, out=offsets[1:])
+    total = int(offsets[-1])
+    centre = rng.uniform(-1.0, 1.0, size=(n_lp, 2))
+    theta = rng.uniform(0.0, 2.0 * math.pi, size=total)
+    r = rng.uniform(0.5, 2.0, size=total)
+    phi = rng.uniform(0.0, 2.0 * math.pi, size=n_lp)
+    owner = np.repeat(np.arange(n_lp, dtype=np.int64), sizes)
+    nx = np.cos(theta)
+    ny = np.sin(theta)
+    del theta
+    b = r + nx * centre[owner, 0] + ny * centre[owner, 1]
+    del r, owner
+    obj = np.stack([np.cos(phi), np.sin(phi)], axis=1).astype(np.float32)
+    return (nx.astype(np.float32), ny.astype(np.float32), b.astype(np.float32), offsets, obj, centre)
+
+
+def _exclusion_constraint(rng, nx, ny, b):
+    """One constraint (a_x, a_y, b) that no point of {n_i . x <= b_i} satisfies.
+
+    nx, ny, b: the LP's stored float32 constraints.  Returns float32 values."""
+    nx64 = nx.astype(np.float64)
+    ny64 = ny.astype(np.float64)
+    b64 = b.astype(np.float64)
+    ang = np.arctan2(ny64, nx64)
+    order = np.argsort(ang, kind="stable")
+    sang = ang[order]
+    m = sang.shape[0]
+    for attempt in range(65):
+        if attempt < 64:
+            psi = rng.uniform(-math.pi, math.pi)
+        else:  # fall back to the middle of the narrowest gap
+            gaps = np.diff(np.concatenate([sang, sang[:1] + 2 * math.pi]))
+            g = int(np.argmin(gaps))
+            psi = sang[g] + 0.5 * gaps[g]
+            psi = (psi + math.pi) % (2 * math.pi) - math.pi
+        k = int(np.searchsorted(sang, psi, side="right"))
+        i = order[(k - 1) % m]
+        j = order[k % m]
+        gap = (ang[j] - ang[i]) % (2 * math.pi)
+        if m == 1 or gap >= math.pi - 1e-9:
+            continue
+        ux, uy = math.cos(psi), math.sin(psi)
+        det = nx64[i] * ny64[j] - ny64[i] * nx64[j]
+        if det == 0.0:
+            if abs(nx64[i] * ux + ny64[i] * uy - 1.0) > 1e-12:
+                continue
+            alpha, beta = 1.0, 0.0
+        else:
+            alpha = (ux * ny64[j] - uy * nx64[j]) / det
+            beta = (nx64[i] * uy - ny64[i] * ux) / det
+        if alpha < 0.0 or beta < 0.0:
+            continue
+        h = alpha * b64[i] + beta * b64[j]
+        return np.float32(-ux), np.float32(-uy), np.float32(-(h + 1.0))
+    raise RuntimeError("no bounded direction found for the exclusion constraint")
+
+
+def disk_batch(sizes, seed=DEFAULT_SEED, infeasible_frac=0.0, box=DEFAULT_BOX):
+    """A batch of disk-family LPs with the given constraint counts.
+
+    A fraction ``infeasible_frac`` of the LPs (round(frac * n_lp), chosen by a seeded
+    sample) gets one appended exclusion constraint, so their size is sizes[l] + 1."""
+    sizes = np.asarray(sizes, dtype=np.int64)
+    rng = np.random.default_rng(seed)
+    ax, ay, b, offsets, obj, _centre = _disk_constraints(rng, sizes)
+    n_lp = sizes.shape[0]
+    n_inf = int(round(infeasible_frac * n_lp))
+    infeasible = np.zeros(n_lp, dtype=bool)
+    if n_inf > 0:
+        pick = np.sort(rng.choice(n_lp, size=n_inf, replace=False))
+        infeasible[pick] = True
+        extra = np.zeros((n_inf, 3), dtype=np.float32)
+        for t, l in enumerate(pick):
+            s, e = offsets[l], offsets[l + 1]
+            extra[t] = _exclusion_constraint(rng, ax[s:e], ay[s:e], b[s:e])
+        new_sizes = sizes + infeasible.astype(np.int64)
+        new_off = np.zeros(n_lp + 1, dtype=np.int64)
+        np.cumsum(new_sizes, out=new_off[1:])
+        total = int(new_off[-1])
+        # Destination of each original constraint: shift by the number of extra
+        # slots inserted before its LP.
+        shift = np.repeat(new_off[:-1] - offsets[:-1], sizes)
+        dst = np.arange(offsets[-1], dtype=np.int64) + shift
+        del shift
+        nax = np.empty(total, np.float32)
+        nay = np.empty(total, np.float32)
+        nb = np.empty(total, np.float32)
+        nax[dst] = ax
+        nay[dst] = ay
+        nb[dst] = b
+        del dst
+        slot = new_off[pick + 1] - 1
+        nax[slot] = extra[:, 0]
+        nay[slot] = extra[:, 1]
+        nb[slot] = extra[:, 2]
+        ax, ay, b, offsets = nax, nay, nb, new_off
+    return {
+        "ax": ax, "ay": ay, "b": b, "offsets": offsets, "obj": obj,
+        "box": tuple(float(v) for v in box), "infeasible": infeasible,
+    }
+
+
+def loguniform_sizes(rng, n_lp, lo, hi):
+    """floor(exp(U[ln lo, ln(hi + 1)))) -- integer sizes log-uniform over [lo, hi]."""
+    s = np.floor(np.exp(rng.uniform(math.log(lo), math.log(hi + 1), size=n_lp))).astype(np.int64)
+    return np.clip(s, lo, hi)
+
+
+def collision_batch(n_lp, seed=DEFAULT_SEED, near_parallel_frac=0.05, box=DEFAULT_BOX):
+    """Collision-avoidance-shaped LPs (16-gon speed limit + neighbour half-planes)."""
+    rng = np.random.default_rng(seed)
+    k_nb = rng.integers(10, 101, size=n_lp)
+    sizes = 16 + k_nb
+    offsets = np.zeros(n_lp + 1, dtype=np.int64)
+    np.cumsum(sizes, out=offsets[1:])
+    total = int(offsets[-1])
+    ax = np.empty(total, np.float64)
+    ay = np.empty(total, np.float64)
+    b = np.empty(total, np.float64)
+    radius = rng.uniform(1.0, 2.0, size=n_lp)
+    gon = 2.0 * math.pi * np.arange(16) / 16.0
+    pref = rng.uniform(0.0, 2.0 * math.pi, size=n_lp)
+    for l in range(n_lp):
+        s = int(offsets[l])
+        k = int(k_nb[l])
+        ax[s:s + 16] = np.cos(gon)
+        ay[s:s + 16] = np.sin(gon)
+        b[s:s + 16] = radius[l]
+        p = rng.uniform(-5.0, 5.0, size=(k, 2))
+        nrm = np.linalg.norm(p, axis=1)
+        nrm[nrm == 0.0] = 1.0
+        ang = np.arctan2(p[:, 1] / nrm, p[:, 0] / nrm)
+        near = rng.random(k) < near_parallel_frac
+        for t in np.nonzero(near)[0]:
+            # an earlier constraint of this LP (polygon side or earlier neighbour)
+            src = int(rng.integers(0, 16 + t))
+            base = gon[src] if src < 16 else ang[src - 16]
+            ang[t] = base + rng.uniform(-1e-6, 1e-6)
+        ax[s + 16:s + 16 + k] = np.cos(ang)
+        ay[s + 16:s + 16 + k] = np.sin(ang)
+        b[s + 16:s + 16 + k] = rng.uniform(0.0, 0.5, size=k)
+    obj = np.stack([np.cos(pref), np.sin(pref)], axis=1).astype(np.float32)
+    return {
+        "ax": ax.astype(np.float32), "ay": ay.astype(np.float32), "b": b.astype(np.float32),
+        "offsets": offsets, "obj": obj, "box": tuple(float(v) for v in box),
+        "infeasible": np.zeros(n_lp, dtype=bool),
+    }
+
+
+# ----------------------------------------------------------------- named workloads
+def plain_small(seed=DEFAULT_SEED):
+    """256 LPs x 64 constraints, all feasible."""
+    return disk_batch(np.full(256, 64, dtype=np.int64), seed=seed)
+
+
+def plain_at_scale(seed=DEFAULT_SEED, n_lp=65536, m=256):
+    """65,536 LPs x 256 constraints; 10 % get a 257th constraint that makes them infeasible."""
+    return disk_batch(np.full(n_lp, m, dtype=np.int64), seed=seed, infeasible_frac=0.1)
+
+
+def ragged(seed=DEFAULT_SEED, n_lp=131072, lo=8, hi=2048):
+    """131,072 LPs with sizes log-uniform in [8, 2048]; 10 % infeasible."""
+    size_rng = np.random.default_rng(seed ^ 0x5EED5EED)
+    sizes = loguniform_sizes(size_rng, n_lp, lo, hi)
+    return disk_batch(sizes, seed=seed, infeasible_frac=0.1)
+
+
+def collision(seed=DEFAULT_SEED, n_lp=16384):
+    """16,384 collision-avoidance LPs with 5 % near-parallel neighbour constraints."""
+    return collision_batch(n_lp, seed=seed)
+
+
+WORKLOADS = {
+    "plain_small_256x64": plain_small,
+    "plain_65536x256": plain_at_scale,
+    "ragged_131072_logu8_2048": ragged,
+    "collision_16384": collision,
+}
+
+
+def algorithmic_bytes(batch) -> int:
+    """Bytes one solve must move at minimum: 12 B per constraint read once, plus per
+    LP 8 B objective, 8 B offset, 8 B result point and 4 B status."""
+    n_c = int(batch["offsets"][-1] - batch["offsets"][0])
+    n_lp = int(batch["offsets"].shape[0] - 1)
+    return 12 * n_c + 28 * n_lp
