@@ -1,0 +1,187 @@
+/*
+ * lp2d.h -- C ABI of the GB300 batched 2-D linear-program solver.
+ *
+ * Method: Charlton, Maddock & Richmond, "Two-Dimensional Batch Linear Programming
+ * on the GPU" (arXiv 1902.04995).  Every LP of a batch is
+ *
+ *     maximise  c^T x   subject to   A x <= b,   x in R^2          (Sec. 2.1, Eq. 1, Eq. 2)
+ *
+ * intersected with a bounding box (the +-M constraints of Sec. 2.1), and is solved by
+ * Seidel's randomized incremental algorithm (Sec. 2.1): constraints are visited in a
+ * seeded random order; when the current optimum violates the visited constraint,
+ * the new optimum is found on that constraint's line by a 1-D LP over every earlier
+ * constraint (Eq. 3 and Eq. 4: a max over left bounds and a min over right bounds).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named "device" are CUDA device (or managed) memory owned by the caller.
+ *   The library never frees or retains them beyond the call's stream work.
+ * - Calls are asynchronous and ordered on `stream` (a cudaStream_t; NULL is the
+ *   legacy default stream).  A non-zero return means nothing was enqueued, and
+ *   lp2d_last_error() describes why (thread-local).
+ * - Constraint layout (SoA, float32): constraint i is ax[i]*x + ay[i]*y <= b[i].
+ *   LP l owns constraints offsets[l] .. offsets[l+1]-1 (CSR, int64, non-decreasing;
+ *   offsets[0] need not be 0).  The caller guarantees offsets[n_lp] does not run past
+ *   the ends of ax/ay/b.  An LP with negative size gets status LP2D_BAD_INPUT and
+ *   sets bit LP2D_DEVERR_BAD_OFFSETS of the workspace error word.
+ * - Objectives: obj_xy[2*l], obj_xy[2*l+1] = (c_x, c_y) of LP l, float32.
+ * - Visit order of LP l: a permutation pi_l of 0..m_l-1 seeded with seed + l
+ *   (uint64 wrap-around); see lp2d_visit_order().  Results of generic LPs do not
+ *   depend on the order; the number of 1-D LPs does.
+ * - Per-LP results: out_status[l] (int32) and out_xy[2*l..2*l+1], the optimal
+ *   vertex (float32 for the FP32 precisions, float64 for LP2D_PREC_FP64).
+ *   INFEASIBLE and BAD_INPUT LPs get xy = (NaN, NaN).  An LP with no constraints
+ *   returns the box corner that maximises c, with status BOX_BOUNDED.
+ */
+#ifndef LP2D_H
+#define LP2D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/** CUDA stream handle; identical to cudaStream_t. */
+typedef struct CUstream_st* lp2d_stream_t;
+
+/** Per-LP outcome written to out_status. */
+typedef enum {
+    LP2D_OPTIMAL = 0,     /**< vertex defined by two of the LP's own constraints */
+    LP2D_INFEASIBLE = 1,  /**< the 1-D LP interval became empty (Eq. 3 > Eq. 4), or a
+                               parallel constraint excluded the line (Sec. 2.1) */
+    LP2D_BOX_BOUNDED = 2, /**< a side of the bounding box passes through the vertex */
+    LP2D_BAD_INPUT = 3    /**< NaN/Inf in the LP's data, or a negative size */
+} lp2d_lp_status;
+
+/** Return codes of the entry points. */
+typedef enum {
+    LP2D_OK = 0,
+    LP2D_ERR_INVALID_ARGUMENT = -1,
+    LP2D_ERR_CUDA = -2,
+    LP2D_ERR_TIMEOUT = -3,
+    LP2D_ERR_WORKSPACE = -4,
+    LP2D_ERR_UNSUPPORTED = -5
+} lp2d_err;
+
+/** Bits of the device error word kept in the workspace. */
+enum { LP2D_DEVERR_BAD_OFFSETS = 1, LP2D_DEVERR_WALK_LIMIT = 2 };
+
+/** The bounding box: the +-M constraints of Sec. 2.1 (xmin < xmax, ymin < ymax, finite). */
+typedef struct {
+    float xmin, xmax, ymin, ymax;
+} lp2d_box;
+
+/** Arithmetic of the solve. */
+typedef enum {
+    LP2D_PREC_FP32 = 0,          /**< FP32 throughout; out_xy is float[2*n_lp] */
+    LP2D_PREC_FP32_F64ISECT = 1, /**< FP32, but a 1-D LP work unit whose two normals are
+                                      near-parallel (|det| < tau*|a||a_h|) is computed in
+                                      FP64; out_xy is float[2*n_lp] */
+    LP2D_PREC_FP64 = 2           /**< FP64 arithmetic on the FP32 inputs; out_xy is double[2*n_lp] */
+} lp2d_precision;
+
+/** How LPs are mapped to the GPU. */
+typedef enum {
+    LP2D_SCHED_PERSISTENT = 0, /**< persistent CTAs pull LPs from a device queue; each LP is
+                                    staged in shared memory in visit order and solved by a
+                                    warp (or a 4-warp team for large LPs) */
+    LP2D_SCHED_UNIFORM = 1     /**< one thread per LP, constraints read from global memory
+                                    in visit order (the paper's naive mapping, Sec. 3) */
+} lp2d_schedule;
+
+/** Options for lp2d_solve_batch_ex.  Fill with lp2d_default_options() first. */
+typedef struct {
+    uint64_t seed;          /**< seed_l = seed + l; default 0 */
+    int32_t precision;      /**< lp2d_precision; default LP2D_PREC_FP32 */
+    int32_t schedule;       /**< lp2d_schedule; default LP2D_SCHED_PERSISTENT */
+    int32_t ctas_per_sm;    /**< persistent grid = SMs x this; 0 = occupancy maximum */
+    int32_t chunk_big;      /**< LPs per queue grab by a CTA team; 0 = default */
+    int32_t chunk_small;    /**< LPs per queue grab by a warp; 0 = default */
+    int32_t check_finite;   /**< non-zero: NaN/Inf data gives LP2D_BAD_INPUT; default 1 */
+    float eps;              /**< relative violation tolerance; 0 = 1e-6 (FP32) / 1e-12 (FP64) */
+    float near_parallel_tau;/**< threshold of LP2D_PREC_FP32_F64ISECT; 0 = 1e-3 */
+    int32_t* out_nviol;     /**< optional device int32[n_lp]: number of 1-D LPs solved */
+    int32_t* out_def;       /**< optional device int32[2*n_lp]: ids of the two constraints
+                                 through the returned vertex (>= 0: the LP's own constraint
+                                 index; -1..-4: box side x<=xmax, x>=xmin, y<=ymax, y>=ymin).
+                                 Undefined for INFEASIBLE / BAD_INPUT LPs. */
+} lp2d_options;
+
+/** Fill *opt with the defaults listed above. */
+void lp2d_default_options(lp2d_options* opt);
+
+/**
+ * Bytes of device workspace lp2d_solve_batch_ex takes for this batch size and these
+ * options.  The workspace holds the persistent queue heads and the device error
+ * word; LP2D_SCHED_UNIFORM runs without one (workspace may be NULL) and then reports
+ * bad offsets only through the per-LP status.  It must be zeroed once before its first use
+ * (lp2d_workspace_init); every solve leaves it zeroed again, except the error word,
+ * which accumulates until read by lp2d_read_device_error.  Two solves that run at
+ * the same time must not share a workspace.
+ */
+size_t lp2d_workspace_bytes(int64_t n_lp, const lp2d_options* opt);
+
+/** Zero `bytes` of workspace on `stream` (cudaMemsetAsync).  Returns an lp2d_err. */
+int lp2d_workspace_init(void* workspace, size_t bytes, lp2d_stream_t stream);
+
+/**
+ * Solve a batch with default options (seed 0, FP32, persistent schedule).
+ *
+ * ax, ay, b:   device float32[offsets[n_lp]]   constraints, SoA
+ * offsets:     device int64[n_lp + 1]          CSR row pointers
+ * n_lp:        number of LPs (0: nothing is enqueued, returns LP2D_OK)
+ * obj_xy:      device float32[2*n_lp]          objective per LP
+ * box:         bounding box (by value)
+ * out_xy:      device float32[2*n_lp]          optimal vertex per LP
+ * out_status:  device int32[n_lp]              lp2d_lp_status per LP
+ *
+ * The queue workspace comes from a small per-(device, stream) pool that the library
+ * allocates on the first call for that stream, so the first call on a stream must
+ * not be inside CUDA-graph capture; lp2d_solve_batch_ex with a caller workspace has
+ * no such restriction.  Returns an lp2d_err.
+ */
+int lp2d_solve_batch(const float* ax, const float* ay, const float* b, const int64_t* offsets,
+                     int64_t n_lp, const float* obj_xy, lp2d_box box, float* out_xy,
+                     int32_t* out_status, lp2d_stream_t stream);
+
+/**
+ * Solve a batch with explicit options and a caller-owned workspace (device memory of
+ * at least lp2d_workspace_bytes(n_lp, opt) bytes, 8-byte aligned, zeroed once by
+ * lp2d_workspace_init; optional for LP2D_SCHED_UNIFORM).  Allocates nothing.
+ * out_xy is float32[2*n_lp] for the FP32 precisions and float64[2*n_lp] for
+ * LP2D_PREC_FP64.  opt == NULL means the defaults.  Returns an lp2d_err.
+ */
+int lp2d_solve_batch_ex(const float* ax, const float* ay, const float* b, const int64_t* offsets,
+                        int64_t n_lp, const float* obj_xy, lp2d_box box, void* out_xy,
+                        int32_t* out_status, const lp2d_options* opt, void* workspace,
+                        size_t workspace_bytes, lp2d_stream_t stream);
+
+/**
+ * Write the visit order pi of one LP with m constraints and seed seed_l (the seed of
+ * LP l is seed + l) into device int64 out[m]: out[k] is the index of the constraint
+ * visited at step k.  Runs the same device code the solver uses (Sec. 2.1 asks for a
+ * random visit order; the order is a 4-round balanced Feistel network on
+ * 2*ceil(ceil(log2 m)/2) bits, at least 2, with SplitMix64 round keys and cycle walking).
+ * Returns an lp2d_err.
+ */
+int lp2d_visit_order(uint64_t seed_l, int64_t m, int64_t* out, lp2d_stream_t stream);
+
+/**
+ * Synchronise `stream`, return the device error word accumulated in `workspace`
+ * (LP2D_DEVERR_* bits) through *out_bits, and clear it.  Returns an lp2d_err.
+ */
+int lp2d_read_device_error(void* workspace, lp2d_stream_t stream, uint32_t* out_bits);
+
+/** Message for the last non-OK return on this thread ("" if none). */
+const char* lp2d_last_error(void);
+
+/** Library version string. */
+const char* lp2d_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LP2D_H */

@@ -1,0 +1,248 @@
+// lp2d_api.cu -- the extern "C" entry points declared in include/lp2d.h: argument
+// validation, option defaults, workspace handling and kernel dispatch.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "lp2d.h"
+#include "lp2d_internal.h"
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int ok() {
+    g_last_error[0] = '\0';
+    return LP2D_OK;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+struct DeviceInfo {
+    int sms = 0;
+    int occ_f32 = 0;
+    int occ_f64 = 0;
+};
+
+std::mutex g_mu;
+std::map<int, DeviceInfo> g_devices;
+std::map<std::pair<int, cudaStream_t>, void*> g_stream_ws;
+
+int device_info(DeviceInfo* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto it = g_devices.find(dev);
+    if (it != g_devices.end()) {
+        *out = it->second;
+        return LP2D_OK;
+    }
+    DeviceInfo info;
+    e = cudaDeviceGetAttribute(&info.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "SM count: %s", cudaGetErrorString(e));
+    e = lp2d::persistent_occupancy(false, &info.occ_f32);
+    if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "occupancy (fp32): %s", cudaGetErrorString(e));
+    e = lp2d::persistent_occupancy(true, &info.occ_f64);
+    if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "occupancy (fp64): %s", cudaGetErrorString(e));
+    if (info.occ_f32 < 1 || info.occ_f64 < 1) return fail(LP2D_ERR_CUDA, "persistent kernel cannot be resident");
+    g_devices[dev] = info;
+    *out = info;
+    return LP2D_OK;
+}
+
+bool finite(float v) { return std::isfinite(v); }
+
+}  // namespace
+
+extern "C" {
+
+void lp2d_default_options(lp2d_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->seed = 0;
+    opt->precision = LP2D_PREC_FP32;
+    opt->schedule = LP2D_SCHED_PERSISTENT;
+    opt->ctas_per_sm = 0;
+    opt->chunk_big = 0;
+    opt->chunk_small = 0;
+    opt->check_finite = 1;
+    opt->eps = 0.0f;
+    opt->near_parallel_tau = 0.0f;
+    opt->out_nviol = nullptr;
+    opt->out_def = nullptr;
+}
+
+size_t lp2d_workspace_bytes(int64_t n_lp, const lp2d_options* opt) {
+    (void)n_lp;
+    (void)opt;
+    return sizeof(unsigned long long) * lp2d::kWsWords;
+}
+
+int lp2d_workspace_init(void* workspace, size_t bytes, lp2d_stream_t stream) {
+    if (bytes == 0) return ok();
+    if (!workspace) return fail(LP2D_ERR_INVALID_ARGUMENT, "workspace is NULL");
+    cudaError_t e = cudaMemsetAsync(workspace, 0, bytes, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    return ok();
+}
+
+int lp2d_solve_batch_ex(const float* ax, const float* ay, const float* b, const int64_t* offsets,
+                        int64_t n_lp, const float* obj_xy, lp2d_box box, void* out_xy,
+                        int32_t* out_status, const lp2d_options* opt_in, void* workspace,
+                        size_t workspace_bytes, lp2d_stream_t stream) {
+    lp2d_options opt;
+    if (opt_in) opt = *opt_in;
+    else lp2d_default_options(&opt);
+
+    if (n_lp < 0) return fail(LP2D_ERR_INVALID_ARGUMENT, "n_lp = %lld < 0", (long long)n_lp);
+    if (opt.precision < LP2D_PREC_FP32 || opt.precision > LP2D_PREC_FP64)
+        return fail(LP2D_ERR_INVALID_ARGUMENT, "unknown precision %d", opt.precision);
+    if (opt.schedule != LP2D_SCHED_PERSISTENT && opt.schedule != LP2D_SCHED_UNIFORM)
+        return fail(LP2D_ERR_INVALID_ARGUMENT, "unknown schedule %d", opt.schedule);
+    if (opt.ctas_per_sm < 0 || opt.chunk_big < 0 || opt.chunk_small < 0)
+        return fail(LP2D_ERR_INVALID_ARGUMENT, "negative tuning parameter");
+    if (!(opt.eps >= 0.0f) || !finite(opt.eps) || !(opt.near_parallel_tau >= 0.0f) || !finite(opt.near_parallel_tau))
+        return fail(LP2D_ERR_INVALID_ARGUMENT, "eps / near_parallel_tau must be finite and >= 0");
+    if (!finite(box.xmin) || !finite(box.xmax) || !finite(box.ymin) || !finite(box.ymax) ||
+        !(box.xmin < box.xmax) || !(box.ymin < box.ymax))
+        return fail(LP2D_ERR_INVALID_ARGUMENT, "box must be finite with xmin < xmax and ymin < ymax");
+    if (opt.precision == LP2D_PREC_FP32_F64ISECT)
+        return fail(LP2D_ERR_UNSUPPORTED, "LP2D_PREC_FP32_F64ISECT is not available in this build");
+    if (n_lp == 0) return ok();
+    if (!ax || !ay || !b || !offsets || !obj_xy || !out_xy || !out_status)
+        return fail(LP2D_ERR_INVALID_ARGUMENT, "NULL data pointer");
+    const size_t out_align = (opt.precision == LP2D_PREC_FP64) ? 8 : 4;
+    if (!aligned(ax, 4) || !aligned(ay, 4) || !aligned(b, 4) || !aligned(obj_xy, 4) || !aligned(offsets, 8) ||
+        !aligned(out_xy, out_align) || !aligned(out_status, 4) || (opt.out_nviol && !aligned(opt.out_nviol, 4)) ||
+        (opt.out_def && !aligned(opt.out_def, 4)))
+        return fail(LP2D_ERR_INVALID_ARGUMENT, "misaligned pointer");
+
+    const size_t need = lp2d_workspace_bytes(n_lp, &opt);
+    const bool ws_usable = workspace && workspace_bytes >= need && aligned(workspace, 8);
+    if (opt.schedule == LP2D_SCHED_PERSISTENT) {
+        if (!workspace) return fail(LP2D_ERR_WORKSPACE, "workspace is NULL (need %zu bytes)", need);
+        if (workspace_bytes < need)
+            return fail(LP2D_ERR_WORKSPACE, "workspace has %zu bytes, need %zu", workspace_bytes, need);
+        if (!aligned(workspace, 8)) return fail(LP2D_ERR_WORKSPACE, "workspace must be 8-byte aligned");
+    }
+
+    lp2d::Params p{};
+    p.ax = ax;
+    p.ay = ay;
+    p.b = b;
+    p.offsets = offsets;
+    p.n_lp = n_lp;
+    p.obj = obj_xy;
+    p.xmin = box.xmin;
+    p.xmax = box.xmax;
+    p.ymin = box.ymin;
+    p.ymax = box.ymax;
+    p.seed = opt.seed;
+    p.out_xy = out_xy;
+    p.out_status = out_status;
+    p.out_nviol = opt.out_nviol;
+    p.out_def = opt.out_def;
+    // The uniform schedule needs no queue; it records device errors only when given
+    // a full-size workspace.
+    p.ws = ws_usable ? reinterpret_cast<unsigned long long*>(workspace) : nullptr;
+    p.eps32 = opt.eps > 0.0f ? opt.eps : 1e-6f;
+    p.eps64 = opt.eps > 0.0f ? static_cast<double>(opt.eps) : 1e-12;
+    p.tau = opt.near_parallel_tau > 0.0f ? opt.near_parallel_tau : 1e-3f;
+    p.chunk_big = opt.chunk_big > 0 ? opt.chunk_big : lp2d::kDefaultChunkBig;
+    p.chunk_small = opt.chunk_small > 0 ? opt.chunk_small : lp2d::kDefaultChunkSmall;
+    p.check_finite = opt.check_finite ? 1 : 0;
+
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool fp64 = opt.precision == LP2D_PREC_FP64;
+    cudaError_t e;
+    if (opt.schedule == LP2D_SCHED_UNIFORM) {
+        e = fp64 ? lp2d::launch_uniform_f64(p, s) : lp2d::launch_uniform_f32(p, s);
+    } else {
+        DeviceInfo info;
+        int rc = device_info(&info);
+        if (rc != LP2D_OK) return rc;
+        const int occ = fp64 ? info.occ_f64 : info.occ_f32;
+        const int per_sm = opt.ctas_per_sm > 0 ? (opt.ctas_per_sm < occ ? opt.ctas_per_sm : occ) : occ;
+        long long grid = static_cast<long long>(info.sms) * per_sm;
+        const long long useful = (n_lp + lp2d::kPersistentWarps - 1) / lp2d::kPersistentWarps;
+        if (grid > useful) grid = useful;
+        if (grid < 1) grid = 1;
+        e = fp64 ? lp2d::launch_persistent_f64(p, static_cast<int>(grid), s)
+                 : lp2d::launch_persistent_f32(p, static_cast<int>(grid), s);
+    }
+    if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return ok();
+}
+
+int lp2d_solve_batch(const float* ax, const float* ay, const float* b, const int64_t* offsets,
+                     int64_t n_lp, const float* obj_xy, lp2d_box box, float* out_xy,
+                     int32_t* out_status, lp2d_stream_t stream) {
+    if (n_lp <= 0)
+        return lp2d_solve_batch_ex(ax, ay, b, offsets, n_lp, obj_xy, box, out_xy, out_status, nullptr, nullptr, 0,
+                                   stream);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t bytes = lp2d_workspace_bytes(n_lp, nullptr);
+    void* ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        auto key = std::make_pair(dev, s);
+        auto it = g_stream_ws.find(key);
+        if (it != g_stream_ws.end()) {
+            ws = it->second;
+        } else {
+            e = cudaMalloc(&ws, bytes);
+            if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "workspace cudaMalloc: %s", cudaGetErrorString(e));
+            e = cudaMemsetAsync(ws, 0, bytes, s);
+            if (e != cudaSuccess) {
+                cudaFree(ws);
+                return fail(LP2D_ERR_CUDA, "workspace memset: %s", cudaGetErrorString(e));
+            }
+            g_stream_ws[key] = ws;
+        }
+    }
+    return lp2d_solve_batch_ex(ax, ay, b, offsets, n_lp, obj_xy, box, out_xy, out_status, nullptr, ws, bytes, stream);
+}
+
+int lp2d_visit_order(uint64_t seed_l, int64_t m, int64_t* out, lp2d_stream_t stream) {
+    if (m < 0 || m > 0x7fffffffll) return fail(LP2D_ERR_INVALID_ARGUMENT, "m = %lld out of range", (long long)m);
+    if (m == 0) return ok();
+    if (!out || !aligned(out, 8)) return fail(LP2D_ERR_INVALID_ARGUMENT, "out must be a non-NULL int64 pointer");
+    cudaError_t e = lp2d::launch_visit_order(seed_l, m, out, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "visit order launch: %s", cudaGetErrorString(e));
+    return ok();
+}
+
+int lp2d_read_device_error(void* workspace, lp2d_stream_t stream, uint32_t* out_bits) {
+    if (!workspace || !out_bits) return fail(LP2D_ERR_INVALID_ARGUMENT, "NULL argument");
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned long long* word = reinterpret_cast<unsigned long long*>(workspace) + lp2d::kWsError;
+    unsigned long long host = 0;
+    cudaError_t e = cudaMemcpyAsync(&host, word, sizeof(host), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(word, 0, sizeof(host), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "reading the error word: %s", cudaGetErrorString(e));
+    *out_bits = static_cast<uint32_t>(host);
+    return ok();
+}
+
+const char* lp2d_last_error(void) { return g_last_error; }
+
+const char* lp2d_version(void) { return "lp2d 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,27 @@
+// lp2d_internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lp2d_device.cuh"
+
+namespace lp2d {
+
+// Shapes of the persistent schedule (see lp2d_persistent.cu).
+constexpr int kPersistentWarps = 4;                               // warps per CTA
+constexpr int kCapSmall = 512;                                    // constraints staged per warp
+constexpr int kCapBig = kPersistentWarps * kCapSmall;             // constraints staged per CTA
+constexpr int kDefaultChunkBig = 4;
+constexpr int kDefaultChunkSmall = 2;
+
+// Launchers.  Each returns the cudaError_t of the launch.
+cudaError_t launch_persistent_f32(const Params& p, int grid, cudaStream_t s);
+cudaError_t launch_persistent_f64(const Params& p, int grid, cudaStream_t s);
+cudaError_t launch_uniform_f32(const Params& p, cudaStream_t s);
+cudaError_t launch_uniform_f64(const Params& p, cudaStream_t s);
+cudaError_t launch_visit_order(uint64_t seed, int64_t m, int64_t* out, cudaStream_t s);
+
+// Resident CTAs per SM of the persistent kernels (occupancy calculator).
+cudaError_t persistent_occupancy(bool fp64, int* ctas_per_sm);
+
+}  // namespace lp2d

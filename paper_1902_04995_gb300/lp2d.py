@@ -1,0 +1,202 @@
+"""Python binding of liblp2d.so: argument marshalling only.
+
+Every function here has the name of the C entry point it wraps (without the
+``lp2d_`` prefix) and forwards torch tensors as raw device pointers on the current
+(or given) CUDA stream.  All compute runs in the library's CUDA kernels; there is
+no CPU or PyTorch fallback: importing this module raises if the library has not
+been built (``python -c "import __graft_entry__ as g; g.build()"``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblp2d.so")
+
+OPTIMAL, INFEASIBLE, BOX_BOUNDED, BAD_INPUT = 0, 1, 2, 3
+OK, ERR_INVALID_ARGUMENT, ERR_CUDA, ERR_TIMEOUT, ERR_WORKSPACE, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+PREC_FP32, PREC_FP32_F64ISECT, PREC_FP64 = 0, 1, 2
+SCHED_PERSISTENT, SCHED_UNIFORM = 0, 1
+DEVERR_BAD_OFFSETS, DEVERR_WALK_LIMIT = 1, 2
+
+
+class Box(ctypes.Structure):
+    _fields_ = [("xmin", ctypes.c_float), ("xmax", ctypes.c_float),
+                ("ymin", ctypes.c_float), ("ymax", ctypes.c_float)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("seed", ctypes.c_uint64),
+        ("precision", ctypes.c_int32),
+        ("schedule", ctypes.c_int32),
+        ("ctas_per_sm", ctypes.c_int32),
+        ("chunk_big", ctypes.c_int32),
+        ("chunk_small", ctypes.c_int32),
+        ("check_finite", ctypes.c_int32),
+        ("eps", ctypes.c_float),
+        ("near_parallel_tau", ctypes.c_float),
+        ("out_nviol", ctypes.c_void_p),
+        ("out_def", ctypes.c_void_p),
+    ]
+
+
+class LP2DError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lp2d error {code}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it first (__graft_entry__.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, u64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_size_t
+    lib.lp2d_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.lp2d_default_options.restype = None
+    lib.lp2d_workspace_bytes.argtypes = [i64, ctypes.POINTER(Options)]
+    lib.lp2d_workspace_bytes.restype = sz
+    lib.lp2d_workspace_init.argtypes = [vp, sz, vp]
+    lib.lp2d_workspace_init.restype = ctypes.c_int
+    lib.lp2d_solve_batch.argtypes = [vp, vp, vp, vp, i64, vp, Box, vp, vp, vp]
+    lib.lp2d_solve_batch.restype = ctypes.c_int
+    lib.lp2d_solve_batch_ex.argtypes = [vp, vp, vp, vp, i64, vp, Box, vp, vp, ctypes.POINTER(Options), vp, sz, vp]
+    lib.lp2d_solve_batch_ex.restype = ctypes.c_int
+    lib.lp2d_visit_order.argtypes = [u64, i64, vp, vp]
+    lib.lp2d_visit_order.restype = ctypes.c_int
+    lib.lp2d_read_device_error.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint32)]
+    lib.lp2d_read_device_error.restype = ctypes.c_int
+    lib.lp2d_last_error.argtypes = []
+    lib.lp2d_last_error.restype = ctypes.c_char_p
+    lib.lp2d_version.argtypes = []
+    lib.lp2d_version.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def _check(rc):
+    if rc != OK:
+        raise LP2DError(rc, _lib.lp2d_last_error().decode())
+    return rc
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _need(t, dtype, name, numel=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} has {t.numel()} elements, needs {numel}")
+
+
+def version() -> str:
+    return _lib.lp2d_version().decode()
+
+
+def last_error() -> str:
+    return _lib.lp2d_last_error().decode()
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    _lib.lp2d_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def workspace_bytes(n_lp: int, options: Options | None = None) -> int:
+    return int(_lib.lp2d_workspace_bytes(n_lp, ctypes.byref(options) if options is not None else None))
+
+
+def workspace_init(workspace: torch.Tensor, stream=None):
+    _check(_lib.lp2d_workspace_init(_ptr(workspace), workspace.numel() * workspace.element_size(),
+                                    _stream_handle(stream)))
+
+
+def new_workspace(n_lp: int, options: Options | None = None, device=None, stream=None) -> torch.Tensor:
+    """A zero-initialised workspace tensor of the size the options need (may be empty)."""
+    n = workspace_bytes(n_lp, options)
+    ws = torch.empty(max(n, 8), dtype=torch.uint8, device=device or "cuda")
+    workspace_init(ws, stream)
+    return ws
+
+
+def _validate(ax, ay, b, offsets, obj, out_xy, out_status, out_dtype):
+    n_lp = offsets.numel() - 1
+    if n_lp < 0:
+        raise ValueError("offsets needs n_lp + 1 entries")
+    _need(ax, torch.float32, "ax")
+    _need(ay, torch.float32, "ay", ax.numel())
+    _need(b, torch.float32, "b", ax.numel())
+    _need(offsets, torch.int64, "offsets")
+    _need(obj, torch.float32, "obj_xy", 2 * n_lp)
+    _need(out_xy, out_dtype, "out_xy", 2 * n_lp)
+    _need(out_status, torch.int32, "out_status", n_lp)
+    return n_lp
+
+
+def solve_batch(ax, ay, b, offsets, obj, box, out_xy, out_status, stream=None):
+    """lp2d_solve_batch: default options (seed 0, FP32, persistent schedule)."""
+    n_lp = _validate(ax, ay, b, offsets, obj, out_xy, out_status, torch.float32)
+    _check(_lib.lp2d_solve_batch(_ptr(ax), _ptr(ay), _ptr(b), _ptr(offsets), n_lp, _ptr(obj), Box(*box),
+                                 _ptr(out_xy), _ptr(out_status), _stream_handle(stream)))
+
+
+def solve_batch_ex(ax, ay, b, offsets, obj, box, out_xy, out_status, options: Options | None = None,
+                   workspace: torch.Tensor | None = None, stream=None):
+    """lp2d_solve_batch_ex: explicit options and a caller workspace (see new_workspace)."""
+    opts = options if options is not None else default_options()
+    out_dtype = torch.float64 if opts.precision == PREC_FP64 else torch.float32
+    n_lp = _validate(ax, ay, b, offsets, obj, out_xy, out_status, out_dtype)
+    wbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(_lib.lp2d_solve_batch_ex(_ptr(ax), _ptr(ay), _ptr(b), _ptr(offsets), n_lp, _ptr(obj), Box(*box),
+                                    _ptr(out_xy), _ptr(out_status), ctypes.byref(opts), _ptr(workspace), wbytes,
+                                    _stream_handle(stream)))
+
+
+def visit_order(seed_l: int, m: int, out: torch.Tensor, stream=None):
+    """lp2d_visit_order: out[k] = pi(k) for one LP with m constraints, seed seed_l."""
+    _need(out, torch.int64, "out", m)
+    _check(_lib.lp2d_visit_order(seed_l & (2**64 - 1), m, _ptr(out), _stream_handle(stream)))
+
+
+def read_device_error(workspace: torch.Tensor, stream=None) -> int:
+    bits = ctypes.c_uint32(0)
+    _check(_lib.lp2d_read_device_error(_ptr(workspace), _stream_handle(stream), ctypes.byref(bits)))
+    return int(bits.value)
+
+
+class Solver:
+    """Device-resident solver for one batch layout: holds the workspace and output
+    tensors so that repeated solves (and CUDA-graph capture) allocate nothing."""
+
+    def __init__(self, n_lp: int, options: Options | None = None, device="cuda"):
+        self.options = options if options is not None else default_options()
+        self.n_lp = n_lp
+        out_dtype = torch.float64 if self.options.precision == PREC_FP64 else torch.float32
+        self.out_xy = torch.empty(2 * n_lp, dtype=out_dtype, device=device)
+        self.out_status = torch.empty(n_lp, dtype=torch.int32, device=device)
+        self.workspace = new_workspace(n_lp, self.options, device=device)
+
+    def __call__(self, ax, ay, b, offsets, obj, box, stream=None):
+        solve_batch_ex(ax, ay, b, offsets, obj, box, self.out_xy, self.out_status, self.options,
+                       self.workspace, stream)
+        return self.out_xy, self.out_status

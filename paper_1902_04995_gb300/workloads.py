@@ -105,15 +105,17 @@ def disk_batch(sizes, seed=DEFAULT_SEED, infeasible_frac=0.0, box=DEFAULT_BOX):
     """A batch of disk-family LPs with the given constraint counts.
 
     A fraction ``infeasible_frac`` of the LPs (round(frac * n_lp), chosen by a seeded
-    sample) gets one appended exclusion constraint, so their size is sizes[l] + 1."""
+    sample among the LPs with at least 3 constraints, where a bounded direction always
+    exists) gets one appended exclusion constraint, so their size is sizes[l] + 1."""
     sizes = np.asarray(sizes, dtype=np.int64)
     rng = np.random.default_rng(seed)
     ax, ay, b, offsets, obj, _centre = _disk_constraints(rng, sizes)
     n_lp = sizes.shape[0]
-    n_inf = int(round(infeasible_frac * n_lp))
+    eligible = np.nonzero(sizes >= 3)[0]
+    n_inf = min(int(round(infeasible_frac * n_lp)), eligible.shape[0])
     infeasible = np.zeros(n_lp, dtype=bool)
     if n_inf > 0:
-        pick = np.sort(rng.choice(n_lp, size=n_inf, replace=False))
+        pick = np.sort(eligible[rng.choice(eligible.shape[0], size=n_inf, replace=False)])
         infeasible[pick] = True
         extra = np.zeros((n_inf, 3), dtype=np.float32)
         for t, l in enumerate(pick):

@@ -1,0 +1,99 @@
+"""The C-ABI library builds, loads and exports every entry point include/lp2d.h
+declares; host-side argument checks work without a GPU (no compute calls)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lp2d.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1902_04995_gb300 import build
+
+    build.build()
+    import torch  # noqa: F401
+    from paper_1902_04995_gb300 import lp2d
+
+    return lp2d
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lp2d_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for n in ("lp2d_solve_batch", "lp2d_solve_batch_ex", "lp2d_workspace_bytes", "lp2d_visit_order",
+              "lp2d_last_error", "lp2d_read_device_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    raw = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(raw, n)]
+    assert not missing, missing
+
+
+def test_options_and_workspace_sizes(lib):
+    o = lib.default_options()
+    assert (o.seed, o.precision, o.schedule, o.check_finite) == (0, lib.PREC_FP32, lib.SCHED_PERSISTENT, 1)
+    assert lib.workspace_bytes(1000, o) >= 32
+    assert lib.workspace_bytes(1000, lib.default_options(schedule=lib.SCHED_UNIFORM)) >= 32
+    assert "sm_103a" in lib.version()
+
+
+def test_host_side_validation(lib):
+    L = lib._lib
+    B = lib.Box
+    # n_lp < 0
+    assert L.lp2d_solve_batch_ex(None, None, None, None, -1, None, B(-1, 1, -1, 1), None, None, None, None, 0,
+                                 None) == lib.ERR_INVALID_ARGUMENT
+    assert "n_lp" in lib.last_error()
+    # empty box
+    assert L.lp2d_solve_batch_ex(None, None, None, None, 3, None, B(1, -1, -1, 1), None, None, None, None, 0,
+                                 None) == lib.ERR_INVALID_ARGUMENT
+    # NaN box
+    assert L.lp2d_solve_batch_ex(None, None, None, None, 3, None, B(float("nan"), 1, -1, 1), None, None, None,
+                                 None, 0, None) == lib.ERR_INVALID_ARGUMENT
+    # NULL data
+    assert L.lp2d_solve_batch_ex(None, None, None, None, 3, None, B(-1, 1, -1, 1), None, None, None, None, 0,
+                                 None) == lib.ERR_INVALID_ARGUMENT
+    # unknown precision / schedule
+    o = lib.default_options(precision=7)
+    assert L.lp2d_solve_batch_ex(None, None, None, None, 3, None, B(-1, 1, -1, 1), None, None, ctypes.byref(o),
+                                 None, 0, None) == lib.ERR_INVALID_ARGUMENT
+    o = lib.default_options(schedule=9)
+    assert L.lp2d_solve_batch_ex(None, None, None, None, 3, None, B(-1, 1, -1, 1), None, None, ctypes.byref(o),
+                                 None, 0, None) == lib.ERR_INVALID_ARGUMENT
+    # n_lp == 0 is a no-op
+    assert L.lp2d_solve_batch_ex(None, None, None, None, 0, None, B(-1, 1, -1, 1), None, None, None, None, 0,
+                                 None) == lib.OK
+    # misaligned pointer (never dereferenced: rejected on the host)
+    fake = ctypes.c_void_p(0x1001)
+    assert L.lp2d_solve_batch_ex(fake, fake, fake, fake, 3, fake, B(-1, 1, -1, 1), fake, fake, None, None, 0,
+                                 None) == lib.ERR_INVALID_ARGUMENT
+    # missing workspace for the persistent schedule
+    al = ctypes.c_void_p(0x1000)
+    assert L.lp2d_solve_batch_ex(al, al, al, al, 3, al, B(-1, 1, -1, 1), al, al, None, None, 0,
+                                 None) == lib.ERR_WORKSPACE
+    # visit order size checks
+    assert L.lp2d_visit_order(0, -1, None, None) == lib.ERR_INVALID_ARGUMENT
+    assert L.lp2d_visit_order(0, 0, None, None) == lib.OK
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1902_04995_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "seidel_oracle" not in text, f

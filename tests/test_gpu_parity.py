@@ -1,0 +1,270 @@
+"""GPU parity: the CUDA solver (through the C ABI) against the FP64 CPU oracle on the
+same seeded inputs.  Status is compared bit-exactly; the objective c.x within 1e-4
+relative (FP32) or 1e-10 (FP64), relative to max(|f_oracle|, 1)."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import lp_pins
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+from paper_1902_04995_gb300 import lp2d, workloads  # noqa: E402
+
+TOL = {lp2d.PREC_FP32: 1e-4, lp2d.PREC_FP64: 1e-10}
+THREADS = os.cpu_count() or 1
+DEV = torch.device("cuda:0")
+
+
+def to_dev(batch):
+    return {k: torch.from_numpy(np.ascontiguousarray(batch[k])).to(DEV)
+            for k in ("ax", "ay", "b", "offsets", "obj")}
+
+
+def gpu_solve(batch, seed=0, precision=lp2d.PREC_FP32, schedule=lp2d.SCHED_PERSISTENT, want=False, **tune):
+    t = to_dev(batch)
+    n_lp = len(batch["offsets"]) - 1
+    nviol = torch.full((max(n_lp, 1),), -7, dtype=torch.int32, device=DEV) if want else None
+    dfn = torch.full((max(2 * n_lp, 1),), -7, dtype=torch.int32, device=DEV) if want else None
+    opts = lp2d.default_options(seed=seed, precision=precision, schedule=schedule,
+                                out_nviol=nviol.data_ptr() if want else None,
+                                out_def=dfn.data_ptr() if want else None, **tune)
+    out_dtype = torch.float64 if precision == lp2d.PREC_FP64 else torch.float32
+    xy = torch.full((max(2 * n_lp, 1),), 12345.0, dtype=out_dtype, device=DEV)
+    st = torch.full((max(n_lp, 1),), -9, dtype=torch.int32, device=DEV)
+    ws = lp2d.new_workspace(n_lp, opts, device=DEV)
+    lp2d.solve_batch_ex(t["ax"], t["ay"], t["b"], t["offsets"], t["obj"].reshape(-1), batch["box"], xy, st,
+                        opts, ws)
+    torch.cuda.synchronize()
+    assert lp2d.read_device_error(ws) == 0
+    res = {"xy": xy[:2 * n_lp].cpu().numpy().reshape(-1, 2).astype(np.float64), "status": st[:n_lp].cpu().numpy()}
+    if want:
+        res["nviol"] = nviol[:n_lp].cpu().numpy()
+        res["def"] = dfn[:2 * n_lp].cpu().numpy().reshape(-1, 2)
+    return res
+
+
+def oracle_solve(batch, seed=0, **kw):
+    return oracle.solve_batch(batch["ax"], batch["ay"], batch["b"], batch["offsets"], batch["obj"], batch["box"],
+                              seed=seed, threads=THREADS, **kw)
+
+
+def assert_parity(batch, got, ref, tol):
+    st, rst = got["status"], ref["status"]
+    bad = np.nonzero(st != rst)[0]
+    assert bad.size == 0, f"{bad.size} status mismatches, first LPs {bad[:10]}: gpu {st[bad[:10]]} oracle {rst[bad[:10]]}"
+    c = np.asarray(batch["obj"], np.float64).reshape(-1, 2)
+    solved = (rst == oracle.OPTIMAL) | (rst == oracle.BOX_BOUNDED)
+    f_ref = np.einsum("ij,ij->i", ref["xy"], c)[solved]
+    f_got = np.einsum("ij,ij->i", got["xy"], c)[solved]
+    err = np.abs(f_got - f_ref) / np.maximum(np.abs(f_ref), 1.0)
+    assert err.size == 0 or err.max() <= tol, f"max rel objective error {err.max():.3e} > {tol}"
+    # the returned vertex itself (unique for these generic inputs)
+    scale = np.maximum(np.abs(ref["xy"][solved]).max(axis=1, initial=0), 1.0)
+    verr = np.abs(got["xy"][solved] - ref["xy"][solved]).max(axis=1, initial=0) / scale
+    assert verr.size == 0 or verr.max() <= 50 * tol, f"max rel vertex error {verr.max():.3e}"
+    unsolved = ~solved
+    assert np.isnan(got["xy"][unsolved]).all()
+    return err.max(initial=0.0)
+
+
+# --------------------------------------------------------------- visit order
+@pytest.mark.parametrize("m", [1, 2, 3, 5, 17, 64, 255, 256, 257, 1000, 2048, 4097, 70000])
+def test_visit_order_matches_oracle(m):
+    out = torch.empty(m, dtype=torch.int64, device=DEV)
+    for seed in (0, 5, 2**64 - 3, 20190213 + m):
+        lp2d.visit_order(seed, m, out)
+        torch.cuda.synchronize()
+        assert (out.cpu().numpy() == oracle.perm_array(seed, m)).all()
+
+
+# ------------------------------------------------------------ hand-solved LPs
+@pytest.mark.parametrize("prec,sched", [(lp2d.PREC_FP32, lp2d.SCHED_PERSISTENT), (lp2d.PREC_FP32, lp2d.SCHED_UNIFORM),
+                                        (lp2d.PREC_FP64, lp2d.SCHED_PERSISTENT), (lp2d.PREC_FP64, lp2d.SCHED_UNIFORM)])
+def test_hand_solved_golden(prec, sched):
+    for case in lp_pins.load_hand_lps():
+        cons = np.asarray(case["cons"], np.float32).reshape(-1, 3)
+        batch = {"ax": cons[:, 0].copy(), "ay": cons[:, 1].copy(), "b": cons[:, 2].copy(),
+                 "offsets": np.array([0, len(cons)], np.int64), "obj": np.asarray([case["obj"]], np.float32),
+                 "box": case["box"]}
+        got = gpu_solve(batch, precision=prec, schedule=sched)
+        assert got["status"][0] == case["status"], case["name"]
+        if case["xyf"] is not None:
+            x, y, f = case["xyf"]
+            tol = 1e-5 if prec == lp2d.PREC_FP32 else 1e-12
+            assert abs(got["xy"][0, 0] - x) <= tol * max(1, abs(x)), case["name"]
+            assert abs(got["xy"][0, 1] - y) <= tol * max(1, abs(y)), case["name"]
+
+
+# ------------------------------------------------------------ the workloads
+@pytest.mark.parametrize("prec,sched", [(lp2d.PREC_FP32, lp2d.SCHED_PERSISTENT), (lp2d.PREC_FP32, lp2d.SCHED_UNIFORM),
+                                        (lp2d.PREC_FP64, lp2d.SCHED_PERSISTENT), (lp2d.PREC_FP64, lp2d.SCHED_UNIFORM)])
+def test_plain_small_256x64(prec, sched):
+    batch = workloads.plain_small()
+    got = gpu_solve(batch, seed=11, precision=prec, schedule=sched)
+    ref = oracle_solve(batch, seed=11)
+    assert_parity(batch, got, ref, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", [lp2d.PREC_FP32, lp2d.PREC_FP64])
+def test_plain_65536x256_full(prec):
+    batch = workloads.plain_at_scale()
+    got = gpu_solve(batch, seed=0, precision=prec)
+    ref = oracle_solve(batch, seed=0)
+    assert (ref["status"] == oracle.INFEASIBLE).sum() == 6554
+    assert_parity(batch, got, ref, TOL[prec])
+
+
+def test_ragged_131072_full_fp32():
+    batch = workloads.ragged()
+    got = gpu_solve(batch, seed=0)
+    ref = oracle_solve(batch, seed=0)
+    assert_parity(batch, got, ref, TOL[lp2d.PREC_FP32])
+
+
+def test_ragged_fp64_uniform_slice():
+    batch = workloads.ragged(n_lp=8192)
+    got = gpu_solve(batch, seed=3, precision=lp2d.PREC_FP64, schedule=lp2d.SCHED_UNIFORM)
+    ref = oracle_solve(batch, seed=3)
+    assert_parity(batch, got, ref, TOL[lp2d.PREC_FP64])
+
+
+# ----------------------------------------------------------- control flow
+@pytest.mark.parametrize("sched", [lp2d.SCHED_PERSISTENT, lp2d.SCHED_UNIFORM])
+def test_fp64_violation_counts_and_defining_pair_match_oracle(sched):
+    # Same pi, same FP64 arithmetic: the GPU takes the oracle's exact path.
+    batch = workloads.ragged(n_lp=4096, lo=8, hi=3000)
+    got = gpu_solve(batch, seed=5, precision=lp2d.PREC_FP64, schedule=sched, want=True)
+    ref = oracle_solve(batch, seed=5, want_nviol=True, want_def=True)
+    assert_parity(batch, got, ref, TOL[lp2d.PREC_FP64])
+    assert (got["nviol"] == ref["nviol"]).all()
+    solved = ref["status"] != oracle.INFEASIBLE
+    assert (np.sort(got["def"][solved], 1) == np.sort(ref["def"][solved][:, :2], 1)).all()
+
+
+def test_fp32_defining_pair_matches_oracle():
+    batch = workloads.plain_at_scale(n_lp=8192)
+    got = gpu_solve(batch, seed=1, want=True)
+    ref = oracle_solve(batch, seed=1, want_def=True, want_nviol=True)
+    solved = ref["status"] != oracle.INFEASIBLE
+    same = (np.sort(got["def"][solved], 1) == np.sort(ref["def"][solved][:, :2], 1)).all(1)
+    assert same.mean() == 1.0
+    assert abs(got["nviol"].mean() - ref["nviol"].mean()) < 0.05 * ref["nviol"].mean()
+
+
+def test_results_identical_across_tuning():
+    batch = workloads.ragged(n_lp=20000)
+    base = gpu_solve(batch, seed=2)
+    for tune in ({"ctas_per_sm": 1}, {"ctas_per_sm": 3, "chunk_big": 1, "chunk_small": 1},
+                 {"chunk_big": 16, "chunk_small": 8}):
+        got = gpu_solve(batch, seed=2, **tune)
+        assert (got["status"] == base["status"]).all()
+        assert np.array_equal(got["xy"], base["xy"], equal_nan=True), tune
+
+
+def test_repeated_launches_reuse_workspace_and_graph_replay_is_identical():
+    batch = workloads.ragged(n_lp=30000)
+    t = to_dev(batch)
+    n_lp = len(batch["offsets"]) - 1
+    solver = lp2d.Solver(n_lp, lp2d.default_options(seed=9), device=DEV)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            solver(t["ax"], t["ay"], t["b"], t["offsets"], t["obj"].reshape(-1), batch["box"])
+    s.synchronize()
+    eager = (solver.out_xy.clone(), solver.out_status.clone())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        solver(t["ax"], t["ay"], t["b"], t["offsets"], t["obj"].reshape(-1), batch["box"])
+    solver.out_xy.zero_()
+    solver.out_status.zero_()
+    for _ in range(5):
+        g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(solver.out_status, eager[1])
+    assert torch.equal(torch.nan_to_num(solver.out_xy, nan=7.0), torch.nan_to_num(eager[0], nan=7.0))
+    ref = oracle_solve(batch, seed=9)
+    got = {"xy": solver.out_xy.cpu().numpy().reshape(-1, 2).astype(np.float64), "status": solver.out_status.cpu().numpy()}
+    assert_parity(batch, got, ref, TOL[lp2d.PREC_FP32])
+    assert lp2d.read_device_error(solver.workspace) == 0
+
+
+# ----------------------------------------------------------- edge cases
+def test_ragged_edges_tiles_and_tails():
+    # sizes straddling the warp (32), team (128), per-warp stage (512) and CTA stage
+    # (2048) boundaries, plus LPs beyond the stage that read through pi from HBM.
+    sizes = np.array([0, 1, 2, 3, 4, 31, 32, 33, 63, 64, 65, 127, 128, 129, 511, 512, 513, 2047, 2048, 2049,
+                      3000, 9000], dtype=np.int64)
+    sizes = np.concatenate([sizes, sizes[::-1], sizes])
+    batch = workloads.disk_batch(sizes, seed=4, infeasible_frac=0.3)
+    for prec in (lp2d.PREC_FP32, lp2d.PREC_FP64):
+        for sched in (lp2d.SCHED_PERSISTENT, lp2d.SCHED_UNIFORM):
+            got = gpu_solve(batch, seed=1, precision=prec, schedule=sched)
+            ref = oracle_solve(batch, seed=1)
+            assert_parity(batch, got, ref, TOL[prec])
+
+
+def test_single_huge_lp_reads_through_global_memory():
+    batch = workloads.disk_batch(np.array([60000], np.int64), seed=8, infeasible_frac=1.0)
+    got = gpu_solve(batch, seed=1)
+    ref = oracle_solve(batch, seed=1)
+    assert ref["status"][0] == oracle.INFEASIBLE
+    assert_parity(batch, got, ref, TOL[lp2d.PREC_FP32])
+    batch = workloads.disk_batch(np.array([60000, 5], np.int64), seed=9)
+    assert_parity(batch, gpu_solve(batch, seed=2), oracle_solve(batch, seed=2), TOL[lp2d.PREC_FP32])
+
+
+def test_empty_batch_is_noop():
+    batch = workloads.disk_batch(np.zeros(0, np.int64), seed=1)
+    got = gpu_solve(batch)
+    assert got["status"].size == 0
+
+
+def test_bad_input_and_bad_offsets():
+    batch = workloads.disk_batch(np.array([10, 10, 10, 600, 10], np.int64), seed=3)
+    batch["ax"][3] = np.nan          # LP 0
+    batch["b"][25] = np.inf          # LP 2
+    batch["ay"][40] = -np.inf        # LP 3 (team path)
+    got = gpu_solve(batch)
+    ref = oracle_solve(batch)
+    assert list(ref["status"][[0, 2, 3]]) == [oracle.BAD_INPUT] * 3
+    assert (got["status"] == ref["status"]).all()
+    assert np.isnan(got["xy"][[0, 2, 3]]).all()
+    # a decreasing offset gives that LP BAD_INPUT and sets the device error bit
+    bad = dict(batch)
+    bad["ax"] = np.nan_to_num(batch["ax"]).astype(np.float32)
+    bad["ay"] = np.nan_to_num(batch["ay"]).astype(np.float32)
+    bad["b"] = np.nan_to_num(batch["b"], posinf=1.0).astype(np.float32)
+    off = bad["offsets"].copy()
+    off[2] = off[1] - 3
+    bad["offsets"] = off
+    t = to_dev(bad)
+    n_lp = 5
+    xy = torch.empty(10, dtype=torch.float32, device=DEV)
+    st = torch.empty(5, dtype=torch.int32, device=DEV)
+    ws = lp2d.new_workspace(n_lp, device=DEV)
+    lp2d.solve_batch_ex(t["ax"], t["ay"], t["b"], t["offsets"], t["obj"].reshape(-1), bad["box"], xy, st, None, ws)
+    assert lp2d.read_device_error(ws) & lp2d.DEVERR_BAD_OFFSETS
+    assert st[1].item() == lp2d.BAD_INPUT
+    assert lp2d.read_device_error(ws) == 0  # reading clears it
+
+
+def test_short_form_entry_point():
+    batch = workloads.plain_small(seed=77)
+    t = to_dev(batch)
+    n_lp = len(batch["offsets"]) - 1
+    xy = torch.empty(2 * n_lp, dtype=torch.float32, device=DEV)
+    st = torch.empty(n_lp, dtype=torch.int32, device=DEV)
+    for _ in range(2):
+        lp2d.solve_batch(t["ax"], t["ay"], t["b"], t["offsets"], t["obj"].reshape(-1), batch["box"], xy, st)
+    torch.cuda.synchronize()
+    got = {"xy": xy.cpu().numpy().reshape(-1, 2).astype(np.float64), "status": st.cpu().numpy()}
+    assert_parity(batch, got, oracle_solve(batch, seed=0), TOL[lp2d.PREC_FP32])
