@@ -1,0 +1,391 @@
+"""Benchmark of the batched 2-D Seidel LP solve on GB300.
+
+One step = one solve of the whole ragged batch (131,072 LPs, sizes log-uniform in
+[8, 2048], about 48.3M constraints, 10 % infeasible) by the persistent FP32 kernel,
+replayed from a CUDA graph with the inputs resident in HBM (579 MB > the 129 MB L2,
+so no flush is needed between steps).  Reported beside it, on the same inputs: the
+plain uniform-launch FP64 solver, the end-to-end rate through the C ABI with
+host-resident buffers, and the FP64 CPU oracle on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own batch (seed + rank): weak scaling
+with no collective on the data path; the ranks only meet at barriers and in the
+max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "2-D LPs solved/sec and % HBM roofline (FP32 ragged vs FP64 plain); serve p50/p99 ms"
+UNIT = "LPs/s"
+WORKLOAD = "ragged_131072_logu8_2048"
+KERNEL = "seidel_persistent_kernel<float>"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=20190213)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1902_04995_gb300", "csrc", "*"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch recorded by an ncu capture of the current kernel source,
+    from the summaries under profiles/ (None when no capture matches the source)."""
+    src = kernel_source_hash()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        text = open(path).read()
+        m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", text)
+        m_wl = re.search(r"workload:\s*(\S+)", text)
+        m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
+        if m_hash and m_tr and m_wl and m_hash.group(1) == src and m_wl.group(1) == workload:
+            return int(m_tr.group(1))
+    return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons, with host timestamps."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1, t_wide0):
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        inside = [p for t, p in self.samples if t0 <= t <= t1]
+        window = "timed"
+        if not inside:
+            inside = [p for t, p in self.samples if t_wide0 <= t <= t1 + 0.25]
+            window = "warmup+timed"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "window": "none"}
+        sm = [num(p[1]) for p in inside if num(p[1]) is not None]
+        smax = [num(p[2]) for p in inside if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in inside for i in range(4) if p[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(inside), "window": window}
+
+
+def oracle_rate(batch, max_seconds: float, min_reps: int = 1):
+    """LPs/s of the FP64 oracle on all host cores, repeating the batch until about
+    max_seconds of CPU work; returns (rate, threads, lps_done, seconds)."""
+    import oracle
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    n_lp = len(batch["offsets"]) - 1
+    done, t0, reps = 0, time.perf_counter(), 0
+    while True:
+        oracle.solve_batch(batch["ax"], batch["ay"], batch["b"], batch["offsets"], batch["obj"], batch["box"],
+                           threads=threads)
+        done += n_lp
+        reps += 1
+        el = time.perf_counter() - t0
+        if reps >= min_reps and el >= max_seconds:
+            break
+        if reps >= min_reps and el * (reps + 1) / reps > 3 * max_seconds:
+            break
+    return done / el, threads, done, el
+
+
+def sample_batch(batch, n_lp_sample):
+    """The first n_lp_sample LPs of a batch (the CPU baselines' bounded sample)."""
+    off = batch["offsets"][: n_lp_sample + 1]
+    s, e = int(off[0]), int(off[-1])
+    return {"ax": batch["ax"][s:e], "ay": batch["ay"][s:e], "b": batch["b"][s:e], "offsets": off - s,
+            "obj": batch["obj"][:n_lp_sample], "box": batch["box"]}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on the host cores (rank 0 only)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1902_04995_gb300 import workloads
+
+    batch = workloads.ragged(seed=args.seed)
+    sample = sample_batch(batch, 8192)
+    n_sample = 8192
+    import oracle
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+
+    def step():
+        oracle.solve_batch(sample["ax"], sample["ay"], sample["b"], sample["offsets"], sample["obj"], sample["box"],
+                           threads=threads)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    value = n_sample * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_lps_per_step": n_sample,
+                   "sample_constraints_per_step": int(sample["offsets"][-1])},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"first {n_sample} LPs of the {WORKLOAD} workload per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    from paper_1902_04995_gb300 import lp2d, workloads
+
+    batch = workloads.ragged(seed=args.seed + rank)
+    n_lp = len(batch["offsets"]) - 1
+    n_c = int(batch["offsets"][-1])
+    algo_bytes = workloads.algorithmic_bytes(batch)
+    t = {k: torch.from_numpy(np.ascontiguousarray(batch[k])).to(dev) for k in ("ax", "ay", "b", "offsets", "obj")}
+    obj = t["obj"].reshape(-1)
+    box = batch["box"]
+    stream = torch.cuda.Stream(device=dev)
+
+    # ---- FP32 persistent solve, graph-replayed
+    solver = lp2d.Solver(n_lp, lp2d.default_options(), device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            solver(t["ax"], t["ay"], t["b"], t["offsets"], obj, box)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        solver(t["ax"], t["ay"], t["b"], t["offsets"], obj, box)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local)
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.3)
+    t_wide0 = time.time()
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            graph.replay()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t_on = time.time()
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            graph.replay()
+    e1.record(stream)
+    stream.synchronize()
+    t_off = time.time()
+    barrier()
+    sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = ms
+    if pg is not None:
+        v = torch.tensor([ms], device=dev)
+        pg.all_reduce(v, op=pg.ReduceOp.MAX)
+        ms_max = float(v.item())
+    # sanity: the timed solves produced a full set of statuses
+    st = solver.out_status.cpu().numpy()
+    assert ((st >= 0) & (st <= 3)).all()
+
+    # ---- FP64 plain uniform solver on the same inputs
+    opt64 = lp2d.default_options(precision=lp2d.PREC_FP64, schedule=lp2d.SCHED_UNIFORM)
+    s64 = lp2d.Solver(n_lp, opt64, device=dev)
+    with torch.cuda.stream(stream):
+        s64(t["ax"], t["ay"], t["b"], t["offsets"], obj, box)
+    stream.synchronize()
+    k64 = 3
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(k64):
+            s64(t["ax"], t["ay"], t["b"], t["offsets"], obj, box)
+    f1.record(stream)
+    stream.synchronize()
+    ms64 = f0.elapsed_time(f1) / k64
+    st64 = s64.out_status.cpu().numpy()
+    status_agree = float((st64 == st).mean())
+
+    # ---- end to end through the C ABI with host-resident inputs and results
+    host = {k: torch.from_numpy(np.ascontiguousarray(batch[k])).pin_memory() for k in ("ax", "ay", "b", "offsets", "obj")}
+    hxy = torch.empty(2 * n_lp, dtype=torch.float32).pin_memory()
+    hst = torch.empty(n_lp, dtype=torch.int32).pin_memory()
+    dbuf = {k: torch.empty_like(t[k]) for k in t}
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = hxy.numel() * 4 + hst.numel() * 4
+    k_e2e = max(3, min(args.steps, 20))
+
+    def e2e_step():
+        for k in dbuf:
+            dbuf[k].copy_(host[k], non_blocking=True)
+        lp2d.solve_batch_ex(dbuf["ax"], dbuf["ay"], dbuf["b"], dbuf["offsets"], dbuf["obj"].reshape(-1), box,
+                            solver.out_xy, solver.out_status, solver.options, solver.workspace)
+        hxy.copy_(solver.out_xy, non_blocking=True)
+        hst.copy_(solver.out_status, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    with torch.cuda.stream(stream):
+        e2e_step()
+        barrier()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(k_e2e):
+            e2e_step()
+        g1.record(stream)
+        stream.synchronize()
+    ms_e2e = g0.elapsed_time(g1) / k_e2e
+    if pg is not None:
+        v = torch.tensor([ms_e2e], device=dev)
+        pg.all_reduce(v, op=pg.ReduceOp.MAX)
+        ms_e2e = float(v.item())
+
+    if rank != 0:
+        if pg is not None:
+            pg.barrier()
+            pg.destroy_process_group()
+        return
+
+    # ---- CPU baseline: the oracle on the host cores, bounded sample
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        sample = sample_batch(batch, 32768)
+        rate, threads, done, el = oracle_rate(sample, max_seconds=8.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first 32768 LPs of the {WORKLOAD} workload ({int(sample['offsets'][-1])} constraints), "
+                         f"repeated: {done} LPs in {el:.1f} s on {threads} threads"}
+
+    peak, peak_kind = measured_peaks()
+    achieved = algo_bytes / (ms * 1e-3) / 1e9
+    clocks = sampler.summary(t_on, t_off, t_wide0)
+    line = {
+        "metric": METRIC, "value": n_lp * world / (ms_max * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded disk-family LPs, sizes log-uniform [8,2048], 10% infeasible)",
+        "config": {"workload": WORKLOAD, "n_lp": n_lp, "n_constraints": n_c, "algorithmic_bytes": algo_bytes,
+                   "l2": "inputs 579 MB > 129 MB L2, no flush", "graph": "one solve per CUDA-graph replay",
+                   "parallelism": f"replicas{world}" if world > 1 else "single-gpu", "seed": args.seed},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": f"{peak_kind} copy bandwidth", "traffic": profiled_traffic(WORKLOAD),
+                     "kernel": KERNEL},
+        "fp64_plain": {"value": n_lp / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                       "achieved_gbs": algo_bytes / (ms64 * 1e-3) / 1e9,
+                       "frac": algo_bytes / (ms64 * 1e-3) / 1e9 / peak, "status_agreement_with_fp32": status_agree,
+                       "kernel": "seidel_uniform_kernel<double>"},
+        "e2e": {"value": n_lp * world / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e, "steps": k_e2e},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "gpu_launches": args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

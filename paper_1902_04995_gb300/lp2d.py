@@ -95,6 +95,20 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
 
 
+_dummy = {}
+
+
+def _data_ptr(t):
+    """Pointer for a constraint or objective array; an empty array (a batch whose LPs
+    have no constraints) gets a one-element device buffer instead of NULL."""
+    if t.numel() > 0:
+        return ctypes.c_void_p(t.data_ptr())
+    key = (t.device, t.dtype)
+    if key not in _dummy:
+        _dummy[key] = torch.zeros(4, dtype=t.dtype, device=t.device)
+    return ctypes.c_void_p(_dummy[key].data_ptr())
+
+
 def _need(t, dtype, name, numel=None):
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
@@ -156,8 +170,8 @@ def _validate(ax, ay, b, offsets, obj, out_xy, out_status, out_dtype):
 def solve_batch(ax, ay, b, offsets, obj, box, out_xy, out_status, stream=None):
     """lp2d_solve_batch: default options (seed 0, FP32, persistent schedule)."""
     n_lp = _validate(ax, ay, b, offsets, obj, out_xy, out_status, torch.float32)
-    _check(_lib.lp2d_solve_batch(_ptr(ax), _ptr(ay), _ptr(b), _ptr(offsets), n_lp, _ptr(obj), Box(*box),
-                                 _ptr(out_xy), _ptr(out_status), _stream_handle(stream)))
+    _check(_lib.lp2d_solve_batch(_data_ptr(ax), _data_ptr(ay), _data_ptr(b), _ptr(offsets), n_lp, _data_ptr(obj),
+                                 Box(*box), _data_ptr(out_xy), _data_ptr(out_status), _stream_handle(stream)))
 
 
 def solve_batch_ex(ax, ay, b, offsets, obj, box, out_xy, out_status, options: Options | None = None,
@@ -167,9 +181,9 @@ def solve_batch_ex(ax, ay, b, offsets, obj, box, out_xy, out_status, options: Op
     out_dtype = torch.float64 if opts.precision == PREC_FP64 else torch.float32
     n_lp = _validate(ax, ay, b, offsets, obj, out_xy, out_status, out_dtype)
     wbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
-    _check(_lib.lp2d_solve_batch_ex(_ptr(ax), _ptr(ay), _ptr(b), _ptr(offsets), n_lp, _ptr(obj), Box(*box),
-                                    _ptr(out_xy), _ptr(out_status), ctypes.byref(opts), _ptr(workspace), wbytes,
-                                    _stream_handle(stream)))
+    _check(_lib.lp2d_solve_batch_ex(_data_ptr(ax), _data_ptr(ay), _data_ptr(b), _ptr(offsets), n_lp,
+                                    _data_ptr(obj), Box(*box), _data_ptr(out_xy), _data_ptr(out_status),
+                                    ctypes.byref(opts), _ptr(workspace), wbytes, _stream_handle(stream)))
 
 
 def visit_order(seed_l: int, m: int, out: torch.Tensor, stream=None):
