@@ -159,6 +159,34 @@ int lp2d_solve_batch_ex(const float* ax, const float* ay, const float* b, const 
                         size_t workspace_bytes, lp2d_stream_t stream);
 
 /**
+ * Solve a batch like lp2d_solve_batch_ex, for callers that cannot allocate device
+ * memory (a plugin whose host framework owns every device byte, a real-time loop
+ * that must not allocate once running, a caller with no device allocator at hand).
+ * The paper has no counterpart: this entry point is an interface convenience.
+ *
+ * The caller passes only inputs and outputs, as in lp2d_solve_batch_ex.  The queue
+ * scratch is a fixed 256-byte array in the library's device memory, which every GPU
+ * that loads the library keeps until the process exits.  No call of this entry point
+ * calls cudaMalloc, cudaFree or any allocating routine.
+ * - The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current.  Make that first call before
+ *   any stream capture.
+ * - Every call clears the array on `stream` before its solve.  All calls share the
+ *   one array, so calls whose work overlaps on the GPU (other streams, other host
+ *   threads) race: order them on one stream, or use lp2d_solve_batch_ex with separate
+ *   workspaces.
+ * - Options whose workspace exceeds the 256-byte array are rejected with
+ *   LP2D_ERR_UNSUPPORTED (none of this version's options do).
+ * - Device errors show only in the per-LP status (the error word is not readable).
+ *   A non-OK return may still have enqueued the clearing of the library's own array;
+ *   no caller memory is touched.
+ * Returns an lp2d_err.
+ */
+int lp2d_solve_batch_noalloc(const float* ax, const float* ay, const float* b, const int64_t* offsets,
+                             int64_t n_lp, const float* obj_xy, lp2d_box box, void* out_xy,
+                             int32_t* out_status, const lp2d_options* opt, lp2d_stream_t stream);
+
+/**
  * Write the visit order pi of one LP with m constraints and seed seed_l (the seed of
  * LP l is seed + l) into device int64 out[m]: out[k] is the index of the constraint
  * visited at step k.  Runs the same device code the solver uses (Sec. 2.1 asks for a

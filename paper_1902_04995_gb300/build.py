@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblp2d.so")
-SOURCES = ["lp2d_api.cu", "lp2d_persistent.cu", "lp2d_uniform.cu"]
+SOURCES = ["lp2d_api.cu", "lp2d_persistent.cu", "lp2d_uniform.cu", "lp2d_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -67,6 +67,18 @@ bool finite(float v) { return std::isfinite(v); }
 
 }  // namespace
 
+namespace lp2d {
+
+int report_error(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+}  // namespace lp2d
+
 extern "C" {
 
 void lp2d_default_options(lp2d_options* opt) {

@@ -24,4 +24,7 @@ cudaError_t launch_visit_order(uint64_t seed, int64_t m, int64_t* out, cudaStrea
 // Resident CTAs per SM of the persistent kernels (occupancy calculator).
 cudaError_t persistent_occupancy(bool fp64, int* ctas_per_sm);
 
+// Record a message for lp2d_last_error() on this thread and return `code`.
+int report_error(int code, const char* fmt, ...);
+
 }  // namespace lp2d

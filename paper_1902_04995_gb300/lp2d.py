@@ -214,3 +214,25 @@ class Solver:
         solve_batch_ex(ax, ay, b, offsets, obj, box, self.out_xy, self.out_status, self.options,
                        self.workspace, stream)
         return self.out_xy, self.out_status
+
+
+_noalloc_ready = False
+
+
+def solve_batch_noalloc(ax, ay, b, offsets, obj, box, out_xy, out_status, options: Options | None = None,
+                        stream=None):
+    """lp2d_solve_batch_noalloc: like solve_batch_ex, with the library's fixed device
+    scratch array instead of a workspace (for callers that cannot allocate device
+    memory).  Calls that overlap on the GPU race on that array."""
+    global _noalloc_ready
+    if not _noalloc_ready:
+        vp, i64 = ctypes.c_void_p, ctypes.c_int64
+        _lib.lp2d_solve_batch_noalloc.argtypes = [vp, vp, vp, vp, i64, vp, Box, vp, vp, ctypes.POINTER(Options), vp]
+        _lib.lp2d_solve_batch_noalloc.restype = ctypes.c_int
+        _noalloc_ready = True
+    opts = options if options is not None else default_options()
+    out_dtype = torch.float64 if opts.precision == PREC_FP64 else torch.float32
+    n_lp = _validate(ax, ay, b, offsets, obj, out_xy, out_status, out_dtype)
+    _check(_lib.lp2d_solve_batch_noalloc(_data_ptr(ax), _data_ptr(ay), _data_ptr(b), _ptr(offsets), n_lp,
+                                         _data_ptr(obj), Box(*box), _data_ptr(out_xy), _data_ptr(out_status),
+                                         ctypes.byref(opts), _stream_handle(stream)))
