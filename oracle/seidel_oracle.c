@@ -34,7 +34,7 @@
  *     "Ciphers with arbitrary finite domains", CT-RSA 2002).  Round key r is the low
  *     32 bits of output r+1 of SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) seeded
  *     with seed_l = seed + l.  Round function F(R, K) = top h bits of
- *     ((R xor K) * 0x9E3779B1 mod 2^32), h = B/2.
+ *     ((R + K) * 0x9E3779B1 mod 2^32), h = B/2.
  *   - status BOX_BOUNDED: one of the two constraints defining the returned vertex
  *     is a box side.  Inputs with NaN/Inf give BAD_INPUT.
  *
@@ -79,7 +79,7 @@ static void perm_init(oracle_perm* P, uint64_t seed, uint64_t m) {
 }
 
 static uint32_t feistel_round_fn(uint32_t R, uint32_t K, uint32_t h) {
-    uint32_t x = (R ^ K) * 0x9E3779B1u;
+    uint32_t x = (R + K) * 0x9E3779B1u;
     return x >> (32u - h);
 }
 

@@ -173,8 +173,11 @@ int lp2d_solve_batch_ex(const float* ax, const float* ay, const float* b, const 
     p.eps32 = opt.eps > 0.0f ? opt.eps : 1e-6f;
     p.eps64 = opt.eps > 0.0f ? static_cast<double>(opt.eps) : 1e-12;
     p.tau = opt.near_parallel_tau > 0.0f ? opt.near_parallel_tau : 1e-3f;
-    p.chunk_big = opt.chunk_big > 0 ? opt.chunk_big : lp2d::kDefaultChunkBig;
-    p.chunk_small = opt.chunk_small > 0 ? opt.chunk_small : lp2d::kDefaultChunkSmall;
+    p.chunk_big = opt.chunk_big > 0 ? (opt.chunk_big < lp2d::kMaxChunk ? opt.chunk_big : lp2d::kMaxChunk)
+                                    : lp2d::kDefaultChunkBig;
+    p.chunk_small = opt.chunk_small > 0
+                        ? (opt.chunk_small < lp2d::kMaxChunkSmall ? opt.chunk_small : lp2d::kMaxChunkSmall)
+                        : lp2d::kDefaultChunkSmall;
     p.check_finite = opt.check_finite ? 1 : 0;
 
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

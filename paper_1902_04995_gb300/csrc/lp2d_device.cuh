@@ -58,7 +58,7 @@ struct Params {
 // restricted to [0, m) by cycle walking (Black & Rogaway, CT-RSA 2002).  Round key r
 // is the low word of output r+1 of SplitMix64 (Steele, Lea & Flood, OOPSLA 2014)
 // seeded with seed + l; the round function is the top h bits of
-// (R xor K) * 0x9E3779B1 (mod 2^32).
+// (R + K) * 0x9E3779B1 (mod 2^32).
 __device__ __forceinline__ uint64_t splitmix64_output(uint64_t seed, uint32_t r) {
     uint64_t z = seed + static_cast<uint64_t>(r + 1u) * 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -88,7 +88,7 @@ struct VisitOrder {
     }
 
     __device__ __forceinline__ uint32_t f(uint32_t r, uint32_t key) const {
-        return ((r ^ key) * 0x9E3779B1u) >> (32u - h);
+        return ((r + key) * 0x9E3779B1u) >> (32u - h);
     }
 
     // One encryption: four rounds of (L, R) -> (R, L ^ F(R)).

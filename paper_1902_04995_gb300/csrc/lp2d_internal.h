@@ -8,11 +8,13 @@
 namespace lp2d {
 
 // Shapes of the persistent schedule (see lp2d_persistent.cu).
-constexpr int kPersistentWarps = 4;                               // warps per CTA
-constexpr int kCapSmall = 512;                                    // constraints staged per warp
-constexpr int kCapBig = kPersistentWarps * kCapSmall;             // constraints staged per CTA
-constexpr int kDefaultChunkBig = 4;
-constexpr int kDefaultChunkSmall = 2;
+constexpr int kPersistentWarps = 4;   // warps per CTA
+constexpr int kCapSmall = 508;        // largest LP one warp stages (512 slots with the box)
+constexpr int kCapBig = 2044;         // largest LP a CTA stages (2048 slots with the box)
+constexpr int kMaxChunk = 32;         // LPs per queue grab, at most
+constexpr int kMaxChunkSmall = 16;    // a warp grab shares its objectives over 32 lanes
+constexpr int kDefaultChunkBig = 8;
+constexpr int kDefaultChunkSmall = 4;
 
 // Launchers.  Each returns the cudaError_t of the launch.
 cudaError_t launch_persistent_f32(const Params& p, int grid, cudaStream_t s);

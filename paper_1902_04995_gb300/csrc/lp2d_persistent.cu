@@ -2,92 +2,128 @@
 //
 // The paper balances the uneven cost of 1-D LPs by spreading work units over the
 // threads of a block (Sec. 3).  Here the balancing happens at the level of whole LPs:
-// a grid of (SMs x resident CTAs) persistent CTAs pulls LP indices from two device
-// queue heads until both are exhausted.
-//   phase 1: LPs with more than kCapSmall constraints, one at a time per CTA, solved
-//            by all 4 warps as a team (staged in the CTA's 24 KB of shared memory;
-//            LPs above kCapBig read through the visit order from global memory);
-//   phase 2: LPs with at most kCapSmall constraints, one per warp, each warp with
-//            its own quarter of the stage.
-// Big LPs therefore start first and small ones fill the tail.  The last CTA to
-// finish resets the queue heads, so the workspace is ready for the next launch
-// on the same stream without a memset.
+// a grid of (SMs x resident CTAs) persistent CTAs pulls chunks of LP indices from two
+// device queue heads until both are exhausted.
+//   phase 1: LPs with more than kCapWarp constraints, one at a time per CTA: the CTA
+//            stages the LP in its 24 KB of shared memory, warp 0 runs Seidel's
+//            iterations and warps 1..3 join only the long 1-D LPs (LPs above kCapTeam
+//            read through the visit order from global memory instead);
+//   phase 2: LPs with at most kCapWarp constraints, one per warp, each warp with a
+//            quarter of the stage.
+// Large LPs therefore start first and small ones fill the tail.  The last CTA to
+// finish resets the queue heads, so the workspace is ready for the next launch on
+// the same stream without a memset.
 #include "lp2d_internal.h"
 #include "lp2d_solve.cuh"
+#include "lp2d_staged.cuh"
 
 namespace lp2d {
+
+constexpr int kWarpSlots = kCapSmall + kBoxSlots;                // stage slots per warp
+constexpr int kStageSlots = kPersistentWarps * kWarpSlots;      // stage slots per CTA
+static_assert(kStageSlots - kBoxSlots == kCapBig, "team capacity");
+
+template <typename Real>
+__device__ __forceinline__ void write_bad(const Params& P, int64_t lp) {
+    atomicOr(P.ws + kWsError, static_cast<unsigned long long>(kDevErrBadOffsets));
+    P.out_status[lp] = kBadInput;
+    Real* out = reinterpret_cast<Real*>(P.out_xy);
+    out[2 * lp] = out[2 * lp + 1] = real_inf<Real>() - real_inf<Real>();
+}
 
 template <typename Real>
 __global__ void __launch_bounds__(kPersistentWarps * 32)
 seidel_persistent_kernel(const Params P) {
-    __shared__ float sX[kCapBig];
-    __shared__ float sY[kCapBig];
-    __shared__ float sB[kCapBig];
-    __shared__ TeamScratch<kPersistentWarps> sc;
+    __shared__ float sX[kStageSlots];
+    __shared__ float sY[kStageSlots];
+    __shared__ float sB[kStageSlots];
+    __shared__ TeamJob job;
+    __shared__ TeamScratch<kPersistentWarps> sc;  // the read-through-HBM path
     __shared__ long long s_grab;
+    __shared__ long long s_off[kMaxChunk + 1];
+    __shared__ float s_obj[2 * kMaxChunk];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
     unsigned phase = 0;
     unsigned long long* ws = P.ws;
+    bool werr = false;
 
-    // ---- phase 1: large LPs, one CTA team each
+    // ---- phase 1: large LPs, one CTA each
     for (;;) {
-        __syncthreads();  // everyone has read the previous s_grab
+        __syncthreads();  // the previous chunk's s_grab / s_off / stage are no longer read
         if (tid == 0) s_grab = static_cast<long long>(atomicAdd(ws + kWsHeadBig, static_cast<unsigned long long>(P.chunk_big)));
         __syncthreads();
         const long long start = s_grab;
         if (start >= P.n_lp) break;
-        const long long end = min(start + static_cast<long long>(P.chunk_big), static_cast<long long>(P.n_lp));
-        for (long long lp = start; lp < end; ++lp) {
-            const int64_t base = __ldg(P.offsets + lp);
-            const int64_t m = __ldg(P.offsets + lp + 1) - base;
-            if (m <= kCapSmall) continue;  // phase 2 (negative sizes are reported there)
-            if (m > 0x7fffffffll) {
-                if (tid == 0) {
-                    atomicOr(ws + kWsError, static_cast<unsigned long long>(kDevErrBadOffsets));
-                    P.out_status[lp] = kBadInput;
-                    Real* out = reinterpret_cast<Real*>(P.out_xy);
-                    out[2 * lp] = out[2 * lp + 1] = real_inf<Real>() - real_inf<Real>();
-                }
+        const int cnt = static_cast<int>(min(static_cast<long long>(P.chunk_big), P.n_lp - start));
+        if (tid <= cnt) s_off[tid] = __ldg(P.offsets + start + tid);
+        if (tid < 2 * cnt) s_obj[tid] = __ldg(P.obj + 2 * start + tid);
+        __syncthreads();
+        for (int i = 0; i < cnt; ++i) {
+            const int64_t lp = start + i;
+            const int64_t base = s_off[i];
+            const int64_t mm = s_off[i + 1] - base;
+            if (mm <= kCapSmall) continue;  // phase 2 (negative sizes are reported there)
+            if (mm > 0x7fffffffll) {
+                if (tid == 0) write_bad<Real>(P, lp);
                 continue;
             }
-            if (m <= kCapBig)
-                solve_lp<kPersistentWarps, Real, true>(P, lp, base, static_cast<int>(m), sX, sY, sB, &sc, phase, tid);
+            const int m = static_cast<int>(mm);
+            if (m > kCapBig) {
+                solve_lp<kPersistentWarps, Real, false>(P, lp, base, m, nullptr, nullptr, nullptr, &sc, phase, tid);
+                continue;
+            }
+            VisitOrder vo;
+            warp_visit_order(vo, P.seed + static_cast<uint64_t>(lp), static_cast<uint32_t>(m), lane);
+            if (warp == 0) write_box(P, sX, sY, sB, lane);
+            stage_lp(vo, m, tid, kPersistentWarps * 32, P.ax + base, P.ay + base, P.b + base, sX, sY, sB, werr);
+            cp_async_wait_all();
+            __syncthreads();
+            if (warp == 0)
+                drive_lp<Real>(P, lp, m, s_obj[2 * i], s_obj[2 * i + 1], vo, sX, sY, sB, lane, &job);
             else
-                solve_lp<kPersistentWarps, Real, false>(P, lp, base, static_cast<int>(m), nullptr, nullptr, nullptr, &sc, phase, tid);
+                team_helper<Real>(sX, sY, sB, &job, tid);
+            __syncthreads();
         }
     }
 
     // ---- phase 2: small LPs, one warp each
-    float* wX = sX + warp * kCapSmall;
-    float* wY = sY + warp * kCapSmall;
-    float* wB = sB + warp * kCapSmall;
-    unsigned wphase = 0;
+    float* wX = sX + warp * kWarpSlots;
+    float* wY = sY + warp * kWarpSlots;
+    float* wB = sB + warp * kWarpSlots;
     for (;;) {
         long long start = 0;
         if (lane == 0) start = static_cast<long long>(atomicAdd(ws + kWsHeadSmall, static_cast<unsigned long long>(P.chunk_small)));
         start = __shfl_sync(kFull, start, 0);
         if (start >= P.n_lp) break;
-        const long long end = min(start + static_cast<long long>(P.chunk_small), static_cast<long long>(P.n_lp));
-        for (long long lp = start; lp < end; ++lp) {
-            const int64_t base = __ldg(P.offsets + lp);
-            const int64_t m = __ldg(P.offsets + lp + 1) - base;
-            if (m > kCapSmall) continue;
-            if (m < 0) {
-                if (lane == 0) {
-                    atomicOr(ws + kWsError, static_cast<unsigned long long>(kDevErrBadOffsets));
-                    P.out_status[lp] = kBadInput;
-                    Real* out = reinterpret_cast<Real*>(P.out_xy);
-                    out[2 * lp] = out[2 * lp + 1] = real_inf<Real>() - real_inf<Real>();
-                }
+        const int cnt = static_cast<int>(min(static_cast<long long>(P.chunk_small), P.n_lp - start));
+        const long long off_l = (lane <= cnt) ? __ldg(P.offsets + start + lane) : 0ll;
+        const float obj_l = (lane < 2 * cnt) ? __ldg(P.obj + 2 * start + lane) : 0.0f;
+        for (int i = 0; i < cnt; ++i) {
+            const int64_t lp = start + i;
+            const int64_t base = __shfl_sync(kFull, off_l, i);
+            const int64_t mm = __shfl_sync(kFull, off_l, i + 1) - base;
+            const float cx = __shfl_sync(kFull, obj_l, 2 * i);
+            const float cy = __shfl_sync(kFull, obj_l, 2 * i + 1);
+            if (mm > kCapSmall) continue;
+            if (mm < 0) {
+                if (lane == 0) write_bad<Real>(P, lp);
                 continue;
             }
-            solve_lp<1, Real, true>(P, lp, base, static_cast<int>(m), wX, wY, wB, nullptr, wphase, lane);
+            const int m = static_cast<int>(mm);
+            VisitOrder vo;
+            warp_visit_order(vo, P.seed + static_cast<uint64_t>(lp), static_cast<uint32_t>(m), lane);
+            write_box(P, wX, wY, wB, lane);
+            stage_lp(vo, m, lane, 32, P.ax + base, P.ay + base, P.b + base, wX, wY, wB, werr);
+            cp_async_wait_all();
+            __syncwarp();
+            drive_lp<Real>(P, lp, m, cx, cy, vo, wX, wY, wB, lane, nullptr);
             __syncwarp();  // all lanes are done with the stage before it is overwritten
         }
     }
+    if (werr) atomicOr(ws + kWsError, static_cast<unsigned long long>(kDevErrWalkLimit));
 
     // ---- the last CTA out resets the queue heads for the next launch
     __syncthreads();

@@ -1,0 +1,305 @@
+// lp2d_staged.cuh -- Seidel's method on an LP staged in shared memory, solved by one
+// warp, or by one warp with three helper warps for the long 1-D LPs.
+//
+// Stage layout (per LP, in visit order): slots 0..3 hold the four box sides (the +-M
+// constraints of Sec. 2.1) in the order x <= xmax, -x <= -xmin, y <= ymax, -y <= -ymin;
+// slot 4 + p holds the constraint visited at position p.  A slot index is therefore a
+// visit position shifted by 4, and ties between equal sigma values go to the lowest
+// slot -- the earliest constraint, box first.
+//
+// Staging: each lane takes constraints q = lane, lane + stride, ..., finds the visit
+// position pi^{-1}(q) by cycle walking, and issues asynchronous 4-byte copies
+// (cp.async) from HBM straight to the stage slot.  Global reads stay coalesced; no
+// register holds the data; a lane whose walk ends early moves on to its next
+// constraint instead of idling until the warp's longest walk ends.
+//
+// Iteration (Sec. 2.1): the warp tests 32 consecutive positions against the current
+// optimum at once; the first violated position (ballot) is the next step of serial
+// Seidel, since every earlier position is satisfied.  Its 1-D LP reduces
+// sigma = num/den over slots 0 .. 4+first-1: den > 0 bounds t from the right
+// (Eq. 4, min), den < 0 from the left (Eq. 3, max), den == 0 with num < 0 excludes
+// the line.  Lanes reduce strided slots, then redux.sync reduces (key, slot) pairs.
+#pragma once
+
+#include "lp2d_device.cuh"
+
+namespace lp2d {
+
+constexpr int kBoxSlots = 4;
+
+__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gsrc) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ void named_barrier(int id, int count) {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
+}
+
+// SplitMix64 round keys: lanes 0..3 compute one output each, the warp shares them.
+__device__ __forceinline__ void warp_visit_order(VisitOrder& vo, uint64_t seed, uint32_t m, int lane) {
+    vo.m = m;
+    const uint32_t bits = (m <= 1u) ? 0u : 32u - static_cast<uint32_t>(__clz(static_cast<int>(m - 1u)));
+    vo.h = (bits + 1u) >> 1;
+    if (vo.h < 1u) vo.h = 1u;
+    vo.mask = (1u << vo.h) - 1u;
+    vo.walk_cap = (vo.h >= 16u) ? 0xffffffffu : (1u << (2u * vo.h));
+    const uint32_t mine = static_cast<uint32_t>(splitmix64_output(seed, static_cast<uint32_t>(lane & 3)));
+    vo.k0 = __shfl_sync(kFull, mine, 0);
+    vo.k1 = __shfl_sync(kFull, mine, 1);
+    vo.k2 = __shfl_sync(kFull, mine, 2);
+    vo.k3 = __shfl_sync(kFull, mine, 3);
+}
+
+// Box sides into stage slots 0..3 (lanes 0..3 of the calling warp).
+__device__ __forceinline__ void write_box(const Params& P, float* sX, float* sY, float* sB, int lane) {
+    if (lane < kBoxSlots) {
+        sX[lane] = (lane == 0) ? 1.0f : (lane == 1) ? -1.0f : 0.0f;
+        sY[lane] = (lane == 2) ? 1.0f : (lane == 3) ? -1.0f : 0.0f;
+        sB[lane] = (lane == 0) ? P.xmax : (lane == 1) ? -P.xmin : (lane == 2) ? P.ymax : -P.ymin;
+    }
+}
+
+// Stage constraints q0, q0 + stride, ... (< m) at slots 4 + pi^{-1}(q).  Every lane of
+// the calling warp must call it.  Completion: cp_async_wait_all() then a barrier.
+__device__ __forceinline__ void stage_lp(const VisitOrder& vo, int m, int q0, int stride,
+                                         const float* __restrict__ gax, const float* __restrict__ gay,
+                                         const float* __restrict__ gb, float* sX, float* sY, float* sB,
+                                         bool& werr) {
+    int q = q0;
+    bool act = q < m;
+    uint32_t x = act ? vo.dec(static_cast<uint32_t>(q)) : 0u;
+    uint32_t walk = 0;
+    const uint32_t mu = static_cast<uint32_t>(m);
+    while (__any_sync(kFull, act)) {
+        if (act) {
+            if (m <= 1 || x < mu) {
+                const uint32_t slot = kBoxSlots + ((m <= 1) ? static_cast<uint32_t>(q) : x);
+                cp_async4(sX + slot, gax + q);
+                cp_async4(sY + slot, gay + q);
+                cp_async4(sB + slot, gb + q);
+                q += stride;
+                act = q < m;
+                walk = 0;
+                if (act) x = vo.dec(static_cast<uint32_t>(q));
+            } else if (++walk >= vo.walk_cap) {
+                werr = true;  // unreachable for a bijection; keeps the loop bounded
+                x = static_cast<uint32_t>(q);
+            } else {
+                x = vo.dec(x);
+            }
+        }
+    }
+}
+
+// One lane's share of a 1-D LP: slots j0, j0 + STRIDE, ... below jend.
+template <typename Real, int STRIDE>
+__device__ __forceinline__ void wu_range(const float* __restrict__ sX, const float* __restrict__ sY,
+                                         const float* __restrict__ sB, int j0, int jend, Real p0x, Real p0y,
+                                         Real ux, Real uy, Real& thi, int& phi, Real& tlo, int& plo, bool& par) {
+#pragma unroll 2
+    for (int j = j0; j < jend; j += STRIDE) {
+        const Real gx = sX[j], gy = sY[j], gb = sB[j];
+        const Real den = gx * ux + gy * uy;
+        const Real num = gb - (gx * p0x + gy * p0y);
+        const Real t = real_div<Real>(num, den);
+        if (den > Real(0)) {
+            if (t < thi) { thi = t; phi = j; }
+        } else if (den < Real(0)) {
+            if (t > tlo) { tlo = t; plo = j; }
+        } else if (num < Real(0)) {
+            par = true;
+        }
+    }
+}
+
+// Warp-wide reduction of the 1-D LP state; every lane gets the result.
+template <typename Real>
+__device__ __forceinline__ void warp_reduce_1dlp(Real& thi, int& phi, Real& tlo, int& plo, bool& par) {
+    using KT = KeyOf<Real>;
+    typename KT::type khi = KT::key(thi), klo = KT::key(tlo);
+    warp_min_pair(khi, phi);
+    warp_max_pair(klo, plo);
+    par = __any_sync(kFull, par);
+    thi = KT::val(khi);
+    tlo = KT::val(klo);
+}
+
+// Shared-memory protocol between the driving warp and its helpers.
+struct TeamJob {
+    int cmd;     // kJobRun or kJobDone
+    int fslot;   // slots 0 .. fslot-1 take part
+    double p0x, p0y, ux, uy;
+    long long khi[4], klo[4];
+    int phi[4], plo[4], par[4];
+};
+constexpr int kJobRun = 1;
+constexpr int kJobDone = 2;
+constexpr int kTeamBarJob = 1;   // named barrier: a job (or done) is posted
+constexpr int kTeamBarPart = 2;  // named barrier: the helpers' partial results are posted
+constexpr int kTeamThreads = 128;
+constexpr int kTeamMinSlots = 384;  // shorter 1-D LPs stay with the driving warp
+
+// Helpers (warps 1..3 of the CTA): wait for jobs until the driver posts kJobDone.
+template <typename Real>
+__device__ void team_helper(const float* __restrict__ sX, const float* __restrict__ sY,
+                            const float* __restrict__ sB, TeamJob* job, int tid) {
+    const int warp = tid >> 5, lane = tid & 31;
+    for (;;) {
+        named_barrier(kTeamBarJob, kTeamThreads);
+        if (job->cmd != kJobRun) break;
+        Real thi = real_inf<Real>(), tlo = -real_inf<Real>();
+        int phi = kNoPos, plo = kNoPos;
+        bool par = false;
+        wu_range<Real, kTeamThreads>(sX, sY, sB, tid, job->fslot, static_cast<Real>(job->p0x),
+                                     static_cast<Real>(job->p0y), static_cast<Real>(job->ux),
+                                     static_cast<Real>(job->uy), thi, phi, tlo, plo, par);
+        using KT = KeyOf<Real>;
+        typename KT::type khi = KT::key(thi), klo = KT::key(tlo);
+        warp_min_pair(khi, phi);
+        warp_max_pair(klo, plo);
+        par = __any_sync(kFull, par);
+        if (lane == 0) {
+            job->khi[warp] = static_cast<long long>(khi);
+            job->klo[warp] = static_cast<long long>(klo);
+            job->phi[warp] = phi;
+            job->plo[warp] = plo;
+            job->par[warp] = par ? 1 : 0;
+        }
+        named_barrier(kTeamBarPart, kTeamThreads);
+    }
+}
+
+// Seidel iterations of one staged LP by one warp (lane = 0..31).  With a team
+// (job != nullptr), 1-D LPs over at least kTeamMinSlots slots are shared with the
+// helper warps, and the driver posts kJobDone when it has finished.  Writes the LP's
+// outputs.
+template <typename Real>
+__device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cyf, const VisitOrder& vo,
+                         const float* __restrict__ sX, const float* __restrict__ sY,
+                         const float* __restrict__ sB, int lane, TeamJob* job) {
+    const Real cx = static_cast<Real>(cxf), cy = static_cast<Real>(cyf);
+    const Real eps = (sizeof(Real) == 4) ? Real(P.eps32) : Real(P.eps64);
+    Real vx = (cx >= Real(0)) ? Real(P.xmax) : Real(P.xmin);
+    Real vy = (cy >= Real(0)) ? Real(P.ymax) : Real(P.ymin);
+    Real avx = real_abs(vx), avy = real_abs(vy);
+    int d0 = (cx >= Real(0)) ? 0 : 1;  // slots of the defining pair
+    int d1 = (cy >= Real(0)) ? 2 : 3;
+    int status = -1;
+    int nviol = 0;
+    float fin = 0.0f;
+    int k = 0;
+    while (k < m) {
+        const int p = k + lane;
+        bool viol = false;
+        if (p < m) {
+            const float fx = sX[kBoxSlots + p], fy = sY[kBoxSlots + p], fb = sB[kBoxSlots + p];
+            fin = fmaf(fx, 0.0f, fmaf(fy, 0.0f, fmaf(fb, 0.0f, fin)));
+            const Real gx = fx, gy = fy, gb = fb;
+            const Real s = gx * vx + gy * vy - gb;
+            const Real tol = eps * (real_abs(gx) * avx + real_abs(gy) * avy + real_abs(gb));
+            viol = s > tol;
+        }
+        const unsigned bal = __ballot_sync(kFull, viol);
+        if (bal == 0u) {
+            k += 32;
+            continue;
+        }
+        const int first = k + __ffs(bal) - 1;
+        const int fslot = kBoxSlots + first;
+        k = first + 1;
+        // ---- 1-D LP on the violated line l: lx*x + ly*y = lb
+        const Real lx = sX[fslot], ly = sY[fslot], lb = sB[fslot];
+        const Real nrm2 = lx * lx + ly * ly;
+        if (!(nrm2 != Real(0))) {  // 0.x <= lb < 0 (NaN data also stops here)
+            status = kInfeasible;
+            break;
+        }
+        const Real sc0 = real_div<Real>(lb, nrm2);
+        const Real p0x = lx * sc0, p0y = ly * sc0;  // foot of l
+        const Real ux = -ly, uy = lx;              // direction of l
+        Real thi = real_inf<Real>(), tlo = -real_inf<Real>();
+        int phi = kNoPos, plo = kNoPos;
+        bool par = false;
+        if (job != nullptr && fslot >= kTeamMinSlots) {
+            if (lane == 0) {
+                job->cmd = kJobRun;
+                job->fslot = fslot;
+                job->p0x = static_cast<double>(p0x);
+                job->p0y = static_cast<double>(p0y);
+                job->ux = static_cast<double>(ux);
+                job->uy = static_cast<double>(uy);
+            }
+            named_barrier(kTeamBarJob, kTeamThreads);
+            wu_range<Real, kTeamThreads>(sX, sY, sB, lane, fslot, p0x, p0y, ux, uy, thi, phi, tlo, plo, par);
+            warp_reduce_1dlp<Real>(thi, phi, tlo, plo, par);
+            named_barrier(kTeamBarPart, kTeamThreads);
+            using KT = KeyOf<Real>;
+            typename KT::type khi = KT::key(thi), klo = KT::key(tlo);
+#pragma unroll
+            for (int w = 1; w < 4; ++w) {
+                const auto kh = static_cast<typename KT::type>(job->khi[w]);
+                const int ph = job->phi[w];
+                if (kh < khi || (kh == khi && ph < phi)) { khi = kh; phi = ph; }
+                const auto kl = static_cast<typename KT::type>(job->klo[w]);
+                const int pl = job->plo[w];
+                if (kl > klo || (kl == klo && pl < plo)) { klo = kl; plo = pl; }
+                par = par || (job->par[w] != 0);
+            }
+            thi = KT::val(khi);
+            tlo = KT::val(klo);
+        } else {
+            wu_range<Real, 32>(sX, sY, sB, lane, fslot, p0x, p0y, ux, uy, thi, phi, tlo, plo, par);
+            warp_reduce_1dlp<Real>(thi, phi, tlo, plo, par);
+        }
+        ++nviol;
+        if (par || tlo > thi) {
+            status = kInfeasible;
+            break;
+        }
+        const Real cu = cx * ux + cy * uy;
+        const bool right = cu > Real(0);
+        const Real t = right ? thi : tlo;
+        vx = p0x + t * ux;
+        vy = p0y + t * uy;
+        avx = real_abs(vx);
+        avy = real_abs(vy);
+        d0 = fslot;
+        d1 = right ? phi : plo;
+    }
+    // positions never scanned (the LP stopped early) still take part in the finiteness check
+    if (P.check_finite) {
+        for (int p = k + lane; p < m; p += 32)
+            fin = fmaf(sX[kBoxSlots + p], 0.0f, fmaf(sY[kBoxSlots + p], 0.0f, fmaf(sB[kBoxSlots + p], 0.0f, fin)));
+    }
+    const bool bad_data = P.check_finite && __any_sync(kFull, fin != fin);
+    const bool bad_obj = !(fabsf(cxf) <= 3.402823466e38f) || !(fabsf(cyf) <= 3.402823466e38f);
+    if (job != nullptr) {
+        if (lane == 0) job->cmd = kJobDone;
+        named_barrier(kTeamBarJob, kTeamThreads);
+    }
+    if (lane == 0) {
+        if (bad_data || bad_obj) status = kBadInput;
+        else if (status < 0) status = (d0 < kBoxSlots || d1 < kBoxSlots) ? kBoxBounded : kOptimal;
+        Real* out = reinterpret_cast<Real*>(P.out_xy);
+        if (status == kInfeasible || status == kBadInput) {
+            const Real nan = real_inf<Real>() - real_inf<Real>();
+            out[2 * lp] = nan;
+            out[2 * lp + 1] = nan;
+        } else {
+            out[2 * lp] = vx;
+            out[2 * lp + 1] = vy;
+        }
+        P.out_status[lp] = status;
+        if (P.out_nviol) P.out_nviol[lp] = nviol;
+        if (P.out_def) {
+            bool e2 = false;
+            P.out_def[2 * lp] = def_id(d0 - kBoxSlots, vo, e2);
+            P.out_def[2 * lp + 1] = def_id(d1 - kBoxSlots, vo, e2);
+        }
+    }
+}
+
+}  // namespace lp2d
