@@ -51,7 +51,7 @@ def _load():
     vp = ctypes.c_void_p
     lib.oracle_splitmix64.restype = u64
     lib.oracle_splitmix64.argtypes = [u64, u32]
-    for name in ("oracle_perm_fwd", "oracle_perm_inv", "oracle_feistel_enc"):
+    for name in ("oracle_perm_fwd", "oracle_perm_inv", "oracle_feistel_enc", "oracle_feistel_dec"):
         getattr(lib, name).restype = i64
         getattr(lib, name).argtypes = [u64, i64, i64]
     lib.oracle_feistel_half_bits.restype = i32
@@ -83,6 +83,10 @@ def perm_inv(seed: int, m: int, q: int) -> int:
 
 def feistel_enc(seed: int, m: int, x: int) -> int:
     return int(_load().oracle_feistel_enc(seed & (2**64 - 1), m, x))
+
+
+def feistel_dec(seed: int, m: int, x: int) -> int:
+    return int(_load().oracle_feistel_dec(seed & (2**64 - 1), m, x))
 
 
 def half_bits(m: int) -> int:

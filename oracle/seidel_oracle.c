@@ -29,12 +29,12 @@
  *   - a zero normal (0,0) is infeasible when b < 0 and never violated otherwise.
  *   - violation test: a.x - b > eps * (|a_x x| + |a_y y| + |b|).
  *   - the random visit order (Sec. 2.1 asks for a random order, no generator is
- *     named): pi_l is a 4-round balanced Feistel network on B = max(2,
- *     2*ceil(ceil(log2 m)/2)) bits with cycle walking to [0, m) (Black & Rogaway,
- *     "Ciphers with arbitrary finite domains", CT-RSA 2002).  Round key r is the low
- *     32 bits of output r+1 of SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) seeded
- *     with seed_l = seed + l.  Round function F(R, K) = top h bits of
- *     ((R + K) * 0x9E3779B1 mod 2^32), h = B/2.
+ *     named): the constraints of LP l are visited in increasing order of their key
+ *     E(q), where E is a 4-round balanced Feistel network on B = max(2,
+ *     2*ceil(ceil(log2 m)/2)) bits (a bijection of [0, 2^B), so keys are distinct).
+ *     Round key r is the low 32 bits of output r+1 of SplitMix64 (Steele, Lea &
+ *     Flood, OOPSLA 2014) seeded with seed_l = seed + l.  Round function
+ *     F(R, K) = top h bits of ((R xor K) * 0x9E3779B1 mod 2^32), h = B/2.
  *   - status BOX_BOUNDED: one of the two constraints defining the returned vertex
  *     is a box side.  Inputs with NaN/Inf give BAD_INPUT.
  *
@@ -79,7 +79,7 @@ static void perm_init(oracle_perm* P, uint64_t seed, uint64_t m) {
 }
 
 static uint32_t feistel_round_fn(uint32_t R, uint32_t K, uint32_t h) {
-    uint32_t x = (R + K) * 0x9E3779B1u;
+    uint32_t x = (R ^ K) * 0x9E3779B1u;
     return x >> (32u - h);
 }
 
@@ -112,32 +112,49 @@ static uint64_t feistel_dec(const oracle_perm* P, uint64_t x) {
     return ((uint64_t)L << h) | R;
 }
 
-/* pi(k): the constraint visited at position k.  Cycle walking: re-encrypt until
- * the value falls inside [0, m). */
-static uint64_t perm_fwd(const oracle_perm* P, uint64_t k) {
-    if (P->m <= 1) return k;
-    uint64_t x = feistel_enc(P, k);
-    while (x >= P->m) x = feistel_enc(P, x);
-    return x;
+/* Visit order: sort the constraints by key.  order[k] = pi(k). */
+typedef struct {
+    uint64_t key;
+    int64_t q;
+} keyed;
+
+static int keyed_cmp(const void* a, const void* b) {
+    const keyed* x = (const keyed*)a;
+    const keyed* y = (const keyed*)b;
+    return (x->key > y->key) - (x->key < y->key);
 }
 
-static uint64_t perm_inv(const oracle_perm* P, uint64_t q) {
-    if (P->m <= 1) return q;
-    uint64_t x = feistel_dec(P, q);
-    while (x >= P->m) x = feistel_dec(P, x);
-    return x;
+static void visit_order(const oracle_perm* P, int64_t m, int64_t* order) {
+    if (m <= 0) return;
+    keyed* kq = (keyed*)malloc((size_t)m * sizeof(keyed));
+    for (int64_t q = 0; q < m; q++) {
+        kq[q].key = feistel_enc(P, (uint64_t)q);
+        kq[q].q = q;
+    }
+    qsort(kq, (size_t)m, sizeof(keyed), keyed_cmp);
+    for (int64_t k = 0; k < m; k++) order[k] = kq[k].q;
+    free(kq);
 }
 
 int64_t oracle_perm_fwd(uint64_t seed, int64_t m, int64_t k) {
     oracle_perm P;
     perm_init(&P, seed, (uint64_t)m);
-    return (int64_t)perm_fwd(&P, (uint64_t)k);
+    int64_t* order = (int64_t*)malloc((size_t)(m > 0 ? m : 1) * sizeof(int64_t));
+    visit_order(&P, m, order);
+    int64_t r = order[k];
+    free(order);
+    return r;
 }
 
+/* Position of constraint q: the number of constraints with a smaller key. */
 int64_t oracle_perm_inv(uint64_t seed, int64_t m, int64_t q) {
     oracle_perm P;
     perm_init(&P, seed, (uint64_t)m);
-    return (int64_t)perm_inv(&P, (uint64_t)q);
+    uint64_t kq = feistel_enc(&P, (uint64_t)q);
+    int64_t rank = 0;
+    for (int64_t i = 0; i < m; i++)
+        if (feistel_enc(&P, (uint64_t)i) < kq) rank++;
+    return rank;
 }
 
 /* Raw Feistel encryption on the 2h-bit domain (exposed for bijectivity tests). */
@@ -145,6 +162,13 @@ int64_t oracle_feistel_enc(uint64_t seed, int64_t m, int64_t x) {
     oracle_perm P;
     perm_init(&P, seed, (uint64_t)m);
     return (int64_t)feistel_enc(&P, (uint64_t)x);
+}
+
+/* Inverse Feistel (exposed for tests). */
+int64_t oracle_feistel_dec(uint64_t seed, int64_t m, int64_t x) {
+    oracle_perm P;
+    perm_init(&P, seed, (uint64_t)m);
+    return (int64_t)feistel_dec(&P, (uint64_t)x);
 }
 
 int32_t oracle_feistel_half_bits(int64_t m) {
@@ -156,7 +180,7 @@ int32_t oracle_feistel_half_bits(int64_t m) {
 void oracle_perm_array(uint64_t seed, int64_t m, int64_t* out) {
     oracle_perm P;
     perm_init(&P, seed, (uint64_t)m);
-    for (int64_t k = 0; k < m; k++) out[k] = (int64_t)perm_fwd(&P, (uint64_t)k);
+    visit_order(&P, m, out);
 }
 
 /* ------------------------------------------------------------- one LP solve */
@@ -200,7 +224,7 @@ int32_t oracle_solve_lp(const float* ax, const float* ay, const float* b, int64_
     int64_t* order = (int64_t*)malloc((size_t)(m > 0 ? m : 1) * sizeof(int64_t));
     oracle_perm P;
     perm_init(&P, seed, (uint64_t)m);
-    for (int64_t k = 0; k < m; k++) order[k] = (int64_t)perm_fwd(&P, (uint64_t)k);
+    visit_order(&P, m, order);
 
     /* Start at the box corner that maximises c (the optimum of the box alone). */
     double x0 = (cx >= 0.0) ? box[1] : box[0];

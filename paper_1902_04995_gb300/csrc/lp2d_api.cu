@@ -235,7 +235,7 @@ int lp2d_solve_batch(const float* ax, const float* ay, const float* b, const int
 }
 
 int lp2d_visit_order(uint64_t seed_l, int64_t m, int64_t* out, lp2d_stream_t stream) {
-    if (m < 0 || m > 0x7fffffffll) return fail(LP2D_ERR_INVALID_ARGUMENT, "m = %lld out of range", (long long)m);
+    if (m < 0 || m > (1ll << 26)) return fail(LP2D_ERR_INVALID_ARGUMENT, "m = %lld out of range [0, 2^26]", (long long)m);
     if (m == 0) return ok();
     if (!out || !aligned(out, 8)) return fail(LP2D_ERR_INVALID_ARGUMENT, "out must be a non-NULL int64 pointer");
     cudaError_t e = lp2d::launch_visit_order(seed_l, m, out, reinterpret_cast<cudaStream_t>(stream));

@@ -21,7 +21,6 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Bits of the device error word (same values as LP2D_DEVERR_* in lp2d.h).
 constexpr unsigned kDevErrBadOffsets = 1u;
-constexpr unsigned kDevErrWalkLimit = 2u;
 
 // Workspace words of the persistent schedule.
 constexpr int kWsHeadBig = 0;    // next LP index for CTA teams
@@ -54,11 +53,15 @@ struct Params {
 
 // ------------------------------------------------------------------ visit order
 // A random visit order gives Seidel's method its expected O(m) time (Sec. 2.1).
-// pi_l is a 4-round balanced Feistel network on 2h bits (2h >= ceil(log2 m), h >= 1)
-// restricted to [0, m) by cycle walking (Black & Rogaway, CT-RSA 2002).  Round key r
-// is the low word of output r+1 of SplitMix64 (Steele, Lea & Flood, OOPSLA 2014)
-// seeded with seed + l; the round function is the top h bits of
-// (R + K) * 0x9E3779B1 (mod 2^32).
+// LP l visits its constraints in increasing order of a key E(q): E is a 4-round
+// balanced Feistel network on 2h bits (2h >= ceil(log2 m), h >= 1), a bijection of
+// [0, 4^h), so keys are distinct.  Round key r is the low word of output r+1 of
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) seeded with seed + l; the round
+// function is the top h bits of (R xor K) * 0x9E3779B1 (mod 2^32).
+// Positions follow from keys without any loop: the visit position of q is the
+// number of constraints with a smaller key (a rank in a bitmap of the keys), and
+// scanning the key domain upward, skipping keys whose constraint index is >= m,
+// lists the constraints in visit order.
 __device__ __forceinline__ uint64_t splitmix64_output(uint64_t seed, uint32_t r) {
     uint64_t z = seed + static_cast<uint64_t>(r + 1u) * 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -70,28 +73,32 @@ struct VisitOrder {
     uint32_t k0, k1, k2, k3;
     uint32_t h;      // bits per half
     uint32_t mask;   // (1 << h) - 1
-    uint32_t m;      // number of constraints; m <= 1 is the identity
-    uint32_t walk_cap;
+    uint32_t m;      // number of constraints
 
-    __device__ __forceinline__ void init(uint64_t seed, uint32_t m_) {
+    __device__ __forceinline__ void init_shape(uint32_t m_) {
         m = m_;
-        uint32_t bits = (m_ <= 1u) ? 0u : 32u - static_cast<uint32_t>(__clz(static_cast<int>(m_ - 1u)));
+        const uint32_t bits = (m_ <= 1u) ? 0u : 32u - static_cast<uint32_t>(__clz(static_cast<int>(m_ - 1u)));
         h = (bits + 1u) >> 1;
         if (h < 1u) h = 1u;
         mask = (1u << h) - 1u;  // h <= 16 since m < 2^31
-        // A walk visits each element of the cycle at most once: 4^h steps bound it.
-        walk_cap = (h >= 16u) ? 0xffffffffu : (1u << (2u * h));
+    }
+
+    __device__ __forceinline__ void init(uint64_t seed, uint32_t m_) {
+        init_shape(m_);
         k0 = static_cast<uint32_t>(splitmix64_output(seed, 0));
         k1 = static_cast<uint32_t>(splitmix64_output(seed, 1));
         k2 = static_cast<uint32_t>(splitmix64_output(seed, 2));
         k3 = static_cast<uint32_t>(splitmix64_output(seed, 3));
     }
 
+    // Size of the key domain, 4^h.
+    __device__ __forceinline__ uint64_t domain() const { return 1ull << (2u * h); }
+
     __device__ __forceinline__ uint32_t f(uint32_t r, uint32_t key) const {
-        return ((r + key) * 0x9E3779B1u) >> (32u - h);
+        return ((r ^ key) * 0x9E3779B1u) >> (32u - h);
     }
 
-    // One encryption: four rounds of (L, R) -> (R, L ^ F(R)).
+    // Key of constraint x: four rounds of (L, R) -> (R, L ^ F(R)).
     __device__ __forceinline__ uint32_t enc(uint32_t x) const {
         uint32_t L = x >> h, R = x & mask, t;
         t = L ^ f(R, k0); L = R; R = t;
@@ -101,7 +108,7 @@ struct VisitOrder {
         return (L << h) | R;
     }
 
-    // Inverse: rounds in reverse, (L, R) -> (R ^ F(L), L).
+    // Constraint with key x: rounds in reverse, (L, R) -> (R ^ F(L), L).
     __device__ __forceinline__ uint32_t dec(uint32_t x) const {
         uint32_t L = x >> h, R = x & mask, t;
         t = R ^ f(L, k3); R = L; L = t;
@@ -109,30 +116,6 @@ struct VisitOrder {
         t = R ^ f(L, k1); R = L; L = t;
         t = R ^ f(L, k0); R = L; L = t;
         return (L << h) | R;
-    }
-
-    // pi(k): constraint visited at position k.
-    __device__ __forceinline__ uint32_t fwd(uint32_t k, bool& walk_error) const {
-        if (m <= 1u) return k;
-        uint32_t x = enc(k);
-        uint32_t it = 0;
-        while (x >= m) {
-            if (++it >= walk_cap) { walk_error = true; return k; }
-            x = enc(x);
-        }
-        return x;
-    }
-
-    // pi^{-1}(q): position at which constraint q is visited.
-    __device__ __forceinline__ uint32_t inv(uint32_t q, bool& walk_error) const {
-        if (m <= 1u) return q;
-        uint32_t x = dec(q);
-        uint32_t it = 0;
-        while (x >= m) {
-            if (++it >= walk_cap) { walk_error = true; return q; }
-            x = dec(x);
-        }
-        return x;
     }
 };
 
@@ -214,12 +197,6 @@ __device__ __forceinline__ void box_side(const Params& P, int s, Real& gx, Real&
     gx = (s == 0) ? Real(1) : (s == 1) ? Real(-1) : Real(0);
     gy = (s == 2) ? Real(1) : (s == 3) ? Real(-1) : Real(0);
     gb = (s == 0) ? Real(P.xmax) : (s == 1) ? Real(-P.xmin) : (s == 2) ? Real(P.ymax) : Real(-P.ymin);
-}
-
-// Visit position -> id reported in out_def: constraint index, or -1 - side for the box.
-__device__ __forceinline__ int def_id(int pos, const VisitOrder& vo, bool& werr) {
-    if (pos < 0) return -1 - (pos + 4);
-    return static_cast<int>(vo.fwd(static_cast<uint32_t>(pos), werr));
 }
 
 }  // namespace lp2d

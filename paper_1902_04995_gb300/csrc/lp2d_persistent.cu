@@ -6,8 +6,8 @@
 // device queue heads until both are exhausted.
 //   phase 1: LPs with more than kCapWarp constraints, one at a time per CTA: the CTA
 //            stages the LP in its 24 KB of shared memory, warp 0 runs Seidel's
-//            iterations and warps 1..3 join only the long 1-D LPs (LPs above kCapTeam
-//            read through the visit order from global memory instead);
+//            iterations and warps 1..3 join only the long 1-D LPs (LPs above kCapBig
+//            are read from global memory in visit order instead);
 //   phase 2: LPs with at most kCapWarp constraints, one per warp, each warp with a
 //            quarter of the stage.
 // Large LPs therefore start first and small ones fill the tail.  The last CTA to
@@ -37,8 +37,11 @@ seidel_persistent_kernel(const Params P) {
     __shared__ float sX[kStageSlots];
     __shared__ float sY[kStageSlots];
     __shared__ float sB[kStageSlots];
+    __shared__ unsigned s_bm[kPersistentWarps * 32];  // key bitmaps (32 words per warp, 128 per CTA)
+    __shared__ int s_pre[kPersistentWarps * 32];      // their prefix counts (CTA staging)
+    __shared__ int s_wsum[kPersistentWarps];
     __shared__ TeamJob job;
-    __shared__ TeamScratch<kPersistentWarps> sc;  // the read-through-HBM path
+    __shared__ TeamScratch<kPersistentWarps> sc;  // the read-from-HBM path
     __shared__ long long s_grab;
     __shared__ long long s_off[kMaxChunk + 1];
     __shared__ float s_obj[2 * kMaxChunk];
@@ -48,7 +51,6 @@ seidel_persistent_kernel(const Params P) {
     const int lane = tid & 31;
     unsigned phase = 0;
     unsigned long long* ws = P.ws;
-    bool werr = false;
 
     // ---- phase 1: large LPs, one CTA each
     for (;;) {
@@ -66,23 +68,23 @@ seidel_persistent_kernel(const Params P) {
             const int64_t base = s_off[i];
             const int64_t mm = s_off[i + 1] - base;
             if (mm <= kCapSmall) continue;  // phase 2 (negative sizes are reported there)
-            if (mm > 0x7fffffffll) {
+            if (mm > kMaxKeyPathM) {
                 if (tid == 0) write_bad<Real>(P, lp);
                 continue;
             }
             const int m = static_cast<int>(mm);
             if (m > kCapBig) {
-                solve_lp<kPersistentWarps, Real, false>(P, lp, base, m, nullptr, nullptr, nullptr, &sc, phase, tid);
+                solve_lp_keys<kPersistentWarps, Real>(P, lp, base, m, &sc, phase, tid);
                 continue;
             }
             VisitOrder vo;
             warp_visit_order(vo, P.seed + static_cast<uint64_t>(lp), static_cast<uint32_t>(m), lane);
             if (warp == 0) write_box(P, sX, sY, sB, lane);
-            stage_lp(vo, m, tid, kPersistentWarps * 32, P.ax + base, P.ay + base, P.b + base, sX, sY, sB, werr);
+            stage_lp_team(vo, m, P.ax + base, P.ay + base, P.b + base, sX, sY, sB, s_bm, s_pre, s_wsum, tid);
             cp_async_wait_all();
             __syncthreads();
             if (warp == 0)
-                drive_lp<Real>(P, lp, m, s_obj[2 * i], s_obj[2 * i + 1], vo, sX, sY, sB, lane, &job);
+                drive_lp<Real>(P, lp, m, s_obj[2 * i], s_obj[2 * i + 1], vo, sX, sY, sB, s_bm, lane, &job);
             else
                 team_helper<Real>(sX, sY, sB, &job, tid);
             __syncthreads();
@@ -93,6 +95,7 @@ seidel_persistent_kernel(const Params P) {
     float* wX = sX + warp * kWarpSlots;
     float* wY = sY + warp * kWarpSlots;
     float* wB = sB + warp * kWarpSlots;
+    unsigned* wbm = s_bm + warp * 32;
     for (;;) {
         long long start = 0;
         if (lane == 0) start = static_cast<long long>(atomicAdd(ws + kWsHeadSmall, static_cast<unsigned long long>(P.chunk_small)));
@@ -116,14 +119,13 @@ seidel_persistent_kernel(const Params P) {
             VisitOrder vo;
             warp_visit_order(vo, P.seed + static_cast<uint64_t>(lp), static_cast<uint32_t>(m), lane);
             write_box(P, wX, wY, wB, lane);
-            stage_lp(vo, m, lane, 32, P.ax + base, P.ay + base, P.b + base, wX, wY, wB, werr);
+            stage_lp_warp(vo, m, P.ax + base, P.ay + base, P.b + base, wX, wY, wB, wbm, lane);
             cp_async_wait_all();
             __syncwarp();
-            drive_lp<Real>(P, lp, m, cx, cy, vo, wX, wY, wB, lane, nullptr);
+            drive_lp<Real>(P, lp, m, cx, cy, vo, wX, wY, wB, wbm, lane, nullptr);
             __syncwarp();  // all lanes are done with the stage before it is overwritten
         }
     }
-    if (werr) atomicOr(ws + kWsError, static_cast<unsigned long long>(kDevErrWalkLimit));
 
     // ---- the last CTA out resets the queue heads for the next launch
     __syncthreads();

@@ -1,24 +1,16 @@
-// lp2d_solve.cuh -- one LP solved by a team of W warps (W = 1: a single warp).
+// lp2d_solve.cuh -- one LP too large for the shared-memory stage, solved by a team of
+// W warps reading its constraints from global memory (L1/L2 hold the LP after the
+// first touch).
 //
-// The LP's constraints are staged once from HBM (coalesced, in stored order) into
-// shared memory at their visit positions pi^{-1}(q), so that every later read --
-// the violation scan and every 1-D LP -- is a contiguous shared-memory read in visit
-// order (the paper stages the current line and the per-LP results in shared memory,
-// Sec. 3; here the whole LP is staged, since it is re-read by every 1-D LP).
-//
-// Control flow follows serial Seidel exactly (Sec. 2.1):
-//   * scan: the team tests T = 32 W consecutive visit positions k..k+T-1 against the
-//     current optimum v at once and takes the first violated one (ballot).  Every
-//     position before it is satisfied by v, so serial Seidel would have left v
-//     unchanged there: the trajectory is the serial one.
-//   * 1-D LP on the violated line l (p0 + t u): every earlier constraint h (box sides
-//     at positions -4..-1, then positions 0..k-1) gives sigma = num/den; den > 0 bounds
-//     t from the right (Eq. 4, min), den < 0 from the left (Eq. 3, max), den == 0 with
-//     num < 0 excludes the line.  Each lane reduces its strided share, then the warp
-//     (redux.sync on order-preserving integer keys) and the team (shared memory)
-//     reduce (value, position) pairs, ties going to the earliest position.
-//   * empty interval (left > right) or an excluding parallel constraint: infeasible.
-//     Otherwise t* = right end if c.u > 0, else left end.
+// Visit order without a stage: scanning the key domain of the Feistel permutation
+// upward and skipping keys whose constraint index is >= m lists the constraints in
+// visit order (increasing key), so "the constraints before position k" are "the
+// constraints whose key is below the key of k".  The team scans T = 32 W keys at a
+// time; the first violated one (ballot) is the next step of serial Seidel (Sec. 2.1).
+// Its 1-D LP runs over the box sides (tags 0..3) and every valid key below it
+// (tag 4 + key): den > 0 bounds t from the right (Eq. 4, min), den < 0 from the left
+// (Eq. 3, max), den == 0 with num < 0 excludes the line; ties go to the lowest tag,
+// the earliest constraint.
 #pragma once
 
 #include "lp2d_device.cuh"
@@ -35,12 +27,6 @@ struct TeamScratch {
     int plo[2][W];
     int flag[2][W];
 };
-
-template <int W>
-__device__ __forceinline__ void team_sync() {
-    if constexpr (W == 1) __syncwarp();
-    else __syncthreads();
-}
 
 // Team-wide OR of a predicate.
 template <int W>
@@ -60,7 +46,7 @@ __device__ __forceinline__ bool team_any(bool v, TeamScratch<W>* sc, unsigned& p
     }
 }
 
-// Team-wide minimum of an int (first violated visit position).
+// Team-wide minimum of an int.
 template <int W>
 __device__ __forceinline__ int team_min(int v, TeamScratch<W>* sc, unsigned& phase, int warp, int lane) {
     int w = __reduce_min_sync(kFull, v);
@@ -78,8 +64,8 @@ __device__ __forceinline__ int team_min(int v, TeamScratch<W>* sc, unsigned& pha
     }
 }
 
-// Team-wide reduction of a 1-D LP: (min right key, its position), (max left key,
-// its position), OR of the parallel-exclusion flag.
+// Team-wide reduction of a 1-D LP: (min right key, its tag), (max left key, its
+// tag), OR of the parallel-exclusion flag.
 template <int W, typename K>
 __device__ __forceinline__ void team_reduce_1dlp(K& khi, int& phi, K& klo, int& plo, bool& par,
                                                  TeamScratch<W>* sc, unsigned& phase, int warp, int lane) {
@@ -116,161 +102,103 @@ __device__ __forceinline__ void team_reduce_1dlp(K& khi, int& phi, K& klo, int& 
     }
 }
 
-// Constraint at visit position p: from the shared-memory stage, or (for LPs larger
-// than the stage) straight from global memory through pi.
-template <bool kStaged>
-struct ConstraintSource {
-    const float* __restrict__ X;
-    const float* __restrict__ Y;
-    const float* __restrict__ B;
-    const VisitOrder* vo;
+// Largest LP the key-domain path takes: its tags (4 + key) must fit an int.
+constexpr int64_t kMaxKeyPathM = 1ll << 30;
 
-    template <typename Real>
-    __device__ __forceinline__ void get(int p, Real& gx, Real& gy, Real& gb, bool& werr) const {
-        if constexpr (kStaged) {
-            gx = static_cast<Real>(X[p]);
-            gy = static_cast<Real>(Y[p]);
-            gb = static_cast<Real>(B[p]);
-        } else {
-            const uint32_t q = vo->fwd(static_cast<uint32_t>(p), werr);
-            gx = static_cast<Real>(__ldg(X + q));
-            gy = static_cast<Real>(__ldg(Y + q));
-            gb = static_cast<Real>(__ldg(B + q));
-        }
-    }
-};
-
-// Solve LP `lp` (constraints base .. base+m-1) with a team of W warps; `tid` is the
-// thread's index within the team.  kStaged: stage into sX/sY/sB (capacity >= m);
-// otherwise read through pi from global memory.  Writes the LP's outputs.
-template <int W, typename Real, bool kStaged>
-__device__ void solve_lp(const Params& P, int64_t lp, int64_t base, int m,
-                         float* __restrict__ sX, float* __restrict__ sY, float* __restrict__ sB,
-                         TeamScratch<W>* sc, unsigned& phase, int tid) {
+// Solve LP `lp` (constraints base .. base+m-1, m <= kMaxKeyPathM) with a team of W
+// warps reading global memory; `tid` is the thread's index within the team.
+// Writes the LP's outputs.
+template <int W, typename Real>
+__device__ void solve_lp_keys(const Params& P, int64_t lp, int64_t base, int m, TeamScratch<W>* sc,
+                              unsigned& phase, int tid) {
     constexpr int T = 32 * W;
     using KT = KeyOf<Real>;
     using K = typename KT::type;
     const int lane = tid & 31;
     const int warp = tid >> 5;
+    const float* __restrict__ gax = P.ax + base;
+    const float* __restrict__ gay = P.ay + base;
+    const float* __restrict__ gbb = P.b + base;
 
     VisitOrder vo;
     vo.init(P.seed + static_cast<uint64_t>(lp), static_cast<uint32_t>(m));
-    bool werr = false;
+    const uint32_t dom = static_cast<uint32_t>(vo.domain());  // <= 2^30
     const float cxf = __ldg(P.obj + 2 * lp);
     const float cyf = __ldg(P.obj + 2 * lp + 1);
     const Real cx = static_cast<Real>(cxf), cy = static_cast<Real>(cyf);
 
-    // ---- staging: coalesced loads in stored order, scattered to visit positions.
-    float fin = 0.0f;  // becomes NaN iff some input is NaN or +-Inf
-    if constexpr (kStaged) {
-        const float* __restrict__ gax = P.ax + base;
-        const float* __restrict__ gay = P.ay + base;
-        const float* __restrict__ gb = P.b + base;
-        for (int q0 = tid; q0 < m; q0 += 4 * T) {
-            float x[4], y[4], z[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int q = q0 + u * T;
-                x[u] = y[u] = z[u] = 0.0f;
-                if (q < m) {
-                    x[u] = __ldcs(gax + q);
-                    y[u] = __ldcs(gay + q);
-                    z[u] = __ldcs(gb + q);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int q = q0 + u * T;
-                if (q < m) {
-                    const uint32_t p = vo.inv(static_cast<uint32_t>(q), werr);
-                    sX[p] = x[u];
-                    sY[p] = y[u];
-                    sB[p] = z[u];
-                    fin = fmaf(x[u], 0.0f, fin);
-                    fin = fmaf(y[u], 0.0f, fin);
-                    fin = fmaf(z[u], 0.0f, fin);
-                }
-            }
-        }
-    } else {
-        if (P.check_finite) {
-            for (int q = tid; q < m; q += T) {
-                fin = fmaf(__ldg(P.ax + base + q), 0.0f, fin);
-                fin = fmaf(__ldg(P.ay + base + q), 0.0f, fin);
-                fin = fmaf(__ldg(P.b + base + q), 0.0f, fin);
-            }
-        }
+    float fin = 0.0f;
+    if (P.check_finite) {
+        for (int q = tid; q < m; q += T)
+            fin = fmaf(__ldg(gax + q), 0.0f, fmaf(__ldg(gay + q), 0.0f, fmaf(__ldg(gbb + q), 0.0f, fin)));
     }
-    if (W == 1) __syncwarp();
-    bool bad = team_any<W>(P.check_finite && (fin != fin), sc, phase, warp, lane);  // also the stage barrier
+    bool bad = team_any<W>(fin != fin, sc, phase, warp, lane);
     bad = bad || !(fabsf(cxf) <= 3.402823466e38f) || !(fabsf(cyf) <= 3.402823466e38f);
 
-    const ConstraintSource<kStaged> src{kStaged ? sX : P.ax + base, kStaged ? sY : P.ay + base,
-                                        kStaged ? sB : P.b + base, &vo};
-
-    // ---- Seidel iterations.  Start at the box corner maximising c.
     Real vx = (cx >= Real(0)) ? Real(P.xmax) : Real(P.xmin);
     Real vy = (cy >= Real(0)) ? Real(P.ymax) : Real(P.ymin);
-    int d0 = (cx >= Real(0)) ? -4 : -3;  // visit positions of the defining pair
-    int d1 = (cy >= Real(0)) ? -2 : -1;
+    int d0 = (cx >= Real(0)) ? 0 : 1;  // tags of the defining pair (box sides 0..3)
+    int d1 = (cy >= Real(0)) ? 2 : 3;
     int status = bad ? kBadInput : -1;
     int nviol = 0;
     const Real eps = (sizeof(Real) == 4) ? Real(P.eps32) : Real(P.eps64);
 
-    int k = 0;
-    while (!bad && k < m) {
-        // scan T positions for the first violated one
-        const int p = k + tid;
+    uint32_t e0 = 0;  // next key to scan
+    while (!bad && e0 < dom) {
+        const uint32_t e = e0 + static_cast<uint32_t>(tid);
         bool viol = false;
-        if (p < m) {
-            Real gx, gy, gb;
-            src.get(p, gx, gy, gb, werr);
-            const Real s = gx * vx + gy * vy - gb;
-            const Real tol = eps * (real_abs(gx * vx) + real_abs(gy * vy) + real_abs(gb));
-            viol = s > tol;
+        if (e < dom) {
+            const uint32_t q = vo.dec(e);
+            if (q < static_cast<uint32_t>(m)) {
+                const Real gx = __ldg(gax + q), gy = __ldg(gay + q), gb = __ldg(gbb + q);
+                const Real s = gx * vx + gy * vy - gb;
+                const Real tol = eps * (real_abs(gx * vx) + real_abs(gy * vy) + real_abs(gb));
+                viol = s > tol;
+            }
         }
         const unsigned bal = __ballot_sync(kFull, viol);
-        const int wfirst = bal ? (k + warp * 32 + __ffs(bal) - 1) : kNoPos;
+        const int wfirst = bal ? static_cast<int>(e0) + warp * 32 + __ffs(bal) - 1 : kNoPos;
         const int first = team_min<W>(wfirst, sc, phase, warp, lane);
         if (first == kNoPos) {
-            k += T;
+            e0 += T;
             continue;
         }
-        // ---- 1-D LP on the violated line l: lx*x + ly*y = lb
-        Real lx, ly, lb;
-        src.get(first, lx, ly, lb, werr);
+        const uint32_t lq = vo.dec(static_cast<uint32_t>(first));
+        const Real lx = __ldg(gax + lq), ly = __ldg(gay + lq), lb = __ldg(gbb + lq);
         const Real nrm2 = lx * lx + ly * ly;
-        if (nrm2 == Real(0)) {  // 0.x <= lb < 0
+        if (nrm2 == Real(0)) {
             status = kInfeasible;
-            d0 = first;
             break;
         }
         const Real sc0 = lb / nrm2;
-        const Real p0x = lx * sc0, p0y = ly * sc0;  // foot of l
-        const Real ux = -ly, uy = lx;              // direction of l
+        const Real p0x = lx * sc0, p0y = ly * sc0;
+        const Real ux = -ly, uy = lx;
         Real thi = real_inf<Real>(), tlo = -real_inf<Real>();
         int phi = kNoPos, plo = kNoPos;
         bool par = false;
         if (tid < 4) {
-            Real gx, gy, gb;
-            box_side<Real>(P, tid, gx, gy, gb);
+            const Real gx = (tid == 0) ? Real(1) : (tid == 1) ? Real(-1) : Real(0);
+            const Real gy = (tid == 2) ? Real(1) : (tid == 3) ? Real(-1) : Real(0);
+            const Real gb = (tid == 0) ? Real(P.xmax) : (tid == 1) ? Real(-P.xmin) : (tid == 2) ? Real(P.ymax)
+                                                                                                : Real(-P.ymin);
             const Real den = gx * ux + gy * uy;
             const Real num = gb - (gx * p0x + gy * p0y);
             const Real t = real_div<Real>(num, den);
-            if (den > Real(0)) { thi = t; phi = tid - 4; }
-            else if (den < Real(0)) { tlo = t; plo = tid - 4; }
+            if (den > Real(0)) { thi = t; phi = tid; }
+            else if (den < Real(0)) { tlo = t; plo = tid; }
             else if (num < Real(0)) par = true;
         }
-        for (int j = tid; j < first; j += T) {
-            Real gx, gy, gb;
-            src.get(j, gx, gy, gb, werr);
+        for (int ek = tid; ek < first; ek += T) {
+            const uint32_t g = vo.dec(static_cast<uint32_t>(ek));
+            if (g >= static_cast<uint32_t>(m)) continue;
+            const Real gx = __ldg(gax + g), gy = __ldg(gay + g), gb = __ldg(gbb + g);
             const Real den = gx * ux + gy * uy;
             const Real num = gb - (gx * p0x + gy * p0y);
             const Real t = real_div<Real>(num, den);
             if (den > Real(0)) {
-                if (t < thi) { thi = t; phi = j; }
+                if (t < thi) { thi = t; phi = 4 + ek; }
             } else if (den < Real(0)) {
-                if (t > tlo) { tlo = t; plo = j; }
+                if (t > tlo) { tlo = t; plo = 4 + ek; }
             } else if (num < Real(0)) {
                 par = true;
             }
@@ -282,7 +210,6 @@ __device__ void solve_lp(const Params& P, int64_t lp, int64_t base, int m,
         tlo = KT::val(klo);
         if (par || tlo > thi) {
             status = kInfeasible;
-            d0 = first;
             break;
         }
         const Real cu = cx * ux + cy * uy;
@@ -290,14 +217,13 @@ __device__ void solve_lp(const Params& P, int64_t lp, int64_t base, int m,
         const Real t = right ? thi : tlo;
         vx = p0x + t * ux;
         vy = p0y + t * uy;
-        d0 = first;
+        d0 = 4 + first;
         d1 = right ? phi : plo;
-        k = first + 1;
+        e0 = static_cast<uint32_t>(first) + 1u;
     }
 
-    if (werr && P.ws) atomicOr(P.ws + kWsError, static_cast<unsigned long long>(kDevErrWalkLimit));
     if (tid == 0) {
-        if (status < 0) status = (d0 < 0 || d1 < 0) ? kBoxBounded : kOptimal;
+        if (status < 0) status = (d0 < 4 || d1 < 4) ? kBoxBounded : kOptimal;
         Real* out = reinterpret_cast<Real*>(P.out_xy);
         if (status == kInfeasible || status == kBadInput) {
             const Real nan = real_inf<Real>() - real_inf<Real>();
@@ -310,9 +236,8 @@ __device__ void solve_lp(const Params& P, int64_t lp, int64_t base, int m,
         P.out_status[lp] = status;
         if (P.out_nviol) P.out_nviol[lp] = nviol;
         if (P.out_def) {
-            bool e2 = false;
-            P.out_def[2 * lp] = def_id(d0, vo, e2);
-            P.out_def[2 * lp + 1] = def_id(d1, vo, e2);
+            P.out_def[2 * lp] = d0 < 4 ? -1 - d0 : static_cast<int>(vo.dec(static_cast<uint32_t>(d0 - 4)));
+            P.out_def[2 * lp + 1] = d1 < 4 ? -1 - d1 : static_cast<int>(vo.dec(static_cast<uint32_t>(d1 - 4)));
         }
     }
 }

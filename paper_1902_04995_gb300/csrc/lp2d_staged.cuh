@@ -7,11 +7,12 @@
 // visit position shifted by 4, and ties between equal sigma values go to the lowest
 // slot -- the earliest constraint, box first.
 //
-// Staging: each lane takes constraints q = lane, lane + stride, ..., finds the visit
-// position pi^{-1}(q) by cycle walking, and issues asynchronous 4-byte copies
-// (cp.async) from HBM straight to the stage slot.  Global reads stay coalesced; no
-// register holds the data; a lane whose walk ends early moves on to its next
-// constraint instead of idling until the warp's longest walk ends.
+// Staging: the keys E(q) of all constraints are set in a bitmap of the key domain
+// (one shared-memory atomic OR each); a prefix count of the bitmap words gives every
+// key its rank, which is the constraint's visit position.  Each constraint is then
+// copied from HBM straight to its stage slot by asynchronous 4-byte copies
+// (cp.async): global reads stay coalesced, no register holds the data, and no lane
+// loops longer than another.
 //
 // Iteration (Sec. 2.1): the warp tests 32 consecutive positions against the current
 // optimum at once; the first violated position (ballot) is the next step of serial
@@ -40,12 +41,7 @@ __device__ __forceinline__ void named_barrier(int id, int count) {
 
 // SplitMix64 round keys: lanes 0..3 compute one output each, the warp shares them.
 __device__ __forceinline__ void warp_visit_order(VisitOrder& vo, uint64_t seed, uint32_t m, int lane) {
-    vo.m = m;
-    const uint32_t bits = (m <= 1u) ? 0u : 32u - static_cast<uint32_t>(__clz(static_cast<int>(m - 1u)));
-    vo.h = (bits + 1u) >> 1;
-    if (vo.h < 1u) vo.h = 1u;
-    vo.mask = (1u << vo.h) - 1u;
-    vo.walk_cap = (vo.h >= 16u) ? 0xffffffffu : (1u << (2u * vo.h));
+    vo.init_shape(m);
     const uint32_t mine = static_cast<uint32_t>(splitmix64_output(seed, static_cast<uint32_t>(lane & 3)));
     vo.k0 = __shfl_sync(kFull, mine, 0);
     vo.k1 = __shfl_sync(kFull, mine, 1);
@@ -62,36 +58,107 @@ __device__ __forceinline__ void write_box(const Params& P, float* sX, float* sY,
     }
 }
 
-// Stage constraints q0, q0 + stride, ... (< m) at slots 4 + pi^{-1}(q).  Every lane of
-// the calling warp must call it.  Completion: cp_async_wait_all() then a barrier.
-__device__ __forceinline__ void stage_lp(const VisitOrder& vo, int m, int q0, int stride,
-                                         const float* __restrict__ gax, const float* __restrict__ gay,
-                                         const float* __restrict__ gb, float* sX, float* sY, float* sB,
-                                         bool& werr) {
-    int q = q0;
-    bool act = q < m;
-    uint32_t x = act ? vo.dec(static_cast<uint32_t>(q)) : 0u;
-    uint32_t walk = 0;
-    const uint32_t mu = static_cast<uint32_t>(m);
-    while (__any_sync(kFull, act)) {
-        if (act) {
-            if (m <= 1 || x < mu) {
-                const uint32_t slot = kBoxSlots + ((m <= 1) ? static_cast<uint32_t>(q) : x);
-                cp_async4(sX + slot, gax + q);
-                cp_async4(sY + slot, gay + q);
-                cp_async4(sB + slot, gb + q);
-                q += stride;
-                act = q < m;
-                walk = 0;
-                if (act) x = vo.dec(static_cast<uint32_t>(q));
-            } else if (++walk >= vo.walk_cap) {
-                werr = true;  // unreachable for a bijection; keeps the loop bounded
-                x = static_cast<uint32_t>(q);
-            } else {
-                x = vo.dec(x);
-            }
-        }
+__device__ __forceinline__ int warp_inclusive_scan(int v, int lane) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int n = __shfl_up_sync(kFull, v, off);
+        if (lane >= off) v += n;
     }
+    return v;
+}
+
+__device__ __forceinline__ void stage_copy(int slot, int q, const float* __restrict__ gax,
+                                           const float* __restrict__ gay, const float* __restrict__ gb,
+                                           float* sX, float* sY, float* sB) {
+    cp_async4(sX + slot, gax + q);
+    cp_async4(sY + slot, gay + q);
+    cp_async4(sB + slot, gb + q);
+}
+
+// Warp staging of an LP with m <= 1024 constraints (key domain <= 1024 bits, one
+// bitmap word per lane).  bm: 32 words of shared memory owned by the warp; it keeps
+// the LP's key bitmap afterwards.  Completion: cp_async_wait_all() then __syncwarp().
+__device__ __forceinline__ void stage_lp_warp(const VisitOrder& vo, int m, const float* __restrict__ gax,
+                                              const float* __restrict__ gay, const float* __restrict__ gb,
+                                              float* sX, float* sY, float* sB, unsigned* bm, int lane) {
+    bm[lane] = 0u;
+    __syncwarp();
+    for (int q = lane; q < m; q += 32) {
+        const uint32_t e = vo.enc(static_cast<uint32_t>(q));
+        atomicOr(bm + (e >> 5), 1u << (e & 31u));
+    }
+    __syncwarp();
+    const unsigned w = bm[lane];
+    const int excl = warp_inclusive_scan(__popc(w), lane) - __popc(w);
+    for (int q0 = 0; q0 < m; q0 += 32) {
+        const int q = q0 + lane;
+        const bool valid = q < m;
+        const uint32_t e = vo.enc(static_cast<uint32_t>(valid ? q : 0));
+        const int src = static_cast<int>(e >> 5);
+        const unsigned we = __shfl_sync(kFull, w, src);
+        const int pe = __shfl_sync(kFull, excl, src);
+        if (valid) stage_copy(kBoxSlots + pe + __popc(we & ((1u << (e & 31u)) - 1u)), q, gax, gay, gb, sX, sY, sB);
+    }
+}
+
+// CTA staging (4 warps) of an LP with m <= 4096 constraints (key domain <= 4096 bits,
+// one bitmap word per thread).  bm, pre: 128 words each; wsum: 4 words.  bm keeps
+// the key bitmap afterwards.  Completion: cp_async_wait_all() then __syncthreads().
+__device__ __forceinline__ void stage_lp_team(const VisitOrder& vo, int m, const float* __restrict__ gax,
+                                              const float* __restrict__ gay, const float* __restrict__ gb,
+                                              float* sX, float* sY, float* sB, unsigned* bm, int* pre,
+                                              int* wsum, int tid) {
+    const int lane = tid & 31, warp = tid >> 5;
+    bm[tid] = 0u;
+    __syncthreads();
+    for (int q = tid; q < m; q += 128) {
+        const uint32_t e = vo.enc(static_cast<uint32_t>(q));
+        atomicOr(bm + (e >> 5), 1u << (e & 31u));
+    }
+    __syncthreads();
+    const unsigned w = bm[tid];
+    const int incl = warp_inclusive_scan(__popc(w), lane);
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int base = 0;
+    for (int i = 0; i < warp; ++i) base += wsum[i];
+    pre[tid] = base + incl - __popc(w);
+    __syncthreads();
+    for (int q = tid; q < m; q += 128) {
+        const uint32_t e = vo.enc(static_cast<uint32_t>(q));
+        const int wi = static_cast<int>(e >> 5);
+        stage_copy(kBoxSlots + pre[wi] + __popc(bm[wi] & ((1u << (e & 31u)) - 1u)), q, gax, gay, gb, sX, sY, sB);
+    }
+}
+
+// The key with rank p in a key bitmap of nwords words (warp-wide; every lane gets it).
+__device__ __forceinline__ uint32_t bitmap_select(const unsigned* bm, int nwords, int p, int lane) {
+    int base = 0;
+    for (int c0 = 0; c0 < nwords; c0 += 32) {
+        const unsigned w = (c0 + lane < nwords) ? bm[c0 + lane] : 0u;
+        const int c = __popc(w);
+        const int incl = warp_inclusive_scan(c, lane);
+        const int total = __shfl_sync(kFull, incl, 31);
+        if (p < base + total) {
+            const unsigned bal = __ballot_sync(kFull, p >= base + incl - c && p < base + incl);
+            const int L = __ffs(bal) - 1;
+            unsigned wl = __shfl_sync(kFull, w, L);
+            const int nth = p - base - __shfl_sync(kFull, incl - c, L);
+            for (int i = 0; i < nth; ++i) wl &= wl - 1u;
+            return static_cast<uint32_t>((c0 + L) * 32 + __ffs(wl) - 1);
+        }
+        base += total;
+    }
+    return 0u;
+}
+
+// Constraint id of a stage slot, as reported in out_def: -1 - side for the box,
+// otherwise the index of the constraint staged there.
+__device__ __forceinline__ int slot_id(int slot, const VisitOrder& vo, const unsigned* bm, int lane) {
+    if (slot < kBoxSlots) return -1 - slot;
+    const uint64_t dw = vo.domain() >> 5;
+    const int nwords = dw > 0 ? static_cast<int>(dw) : 1;
+    return static_cast<int>(vo.dec(bitmap_select(bm, nwords, slot - kBoxSlots, lane)));
 }
 
 // One lane's share of a 1-D LP: slots j0, j0 + STRIDE, ... below jend.
@@ -105,13 +172,16 @@ __device__ __forceinline__ void wu_range(const float* __restrict__ sX, const flo
         const Real den = gx * ux + gy * uy;
         const Real num = gb - (gx * p0x + gy * p0y);
         const Real t = real_div<Real>(num, den);
-        if (den > Real(0)) {
-            if (t < thi) { thi = t; phi = j; }
-        } else if (den < Real(0)) {
-            if (t > tlo) { tlo = t; plo = j; }
-        } else if (num < Real(0)) {
-            par = true;
-        }
+        // branch-free: the lanes of a warp see both signs of den
+        const bool pos = den > Real(0);
+        const bool neg = den < Real(0);
+        const bool take_hi = pos && (t < thi);
+        const bool take_lo = neg && (t > tlo);
+        thi = take_hi ? t : thi;
+        phi = take_hi ? j : phi;
+        tlo = take_lo ? t : tlo;
+        plo = take_lo ? j : plo;
+        par = par || (!pos && !neg && num < Real(0));
     }
 }
 
@@ -179,7 +249,7 @@ __device__ void team_helper(const float* __restrict__ sX, const float* __restric
 template <typename Real>
 __device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cyf, const VisitOrder& vo,
                          const float* __restrict__ sX, const float* __restrict__ sY,
-                         const float* __restrict__ sB, int lane, TeamJob* job) {
+                         const float* __restrict__ sB, const unsigned* bm, int lane, TeamJob* job) {
     const Real cx = static_cast<Real>(cxf), cy = static_cast<Real>(cyf);
     const Real eps = (sizeof(Real) == 4) ? Real(P.eps32) : Real(P.eps64);
     Real vx = (cx >= Real(0)) ? Real(P.xmax) : Real(P.xmin);
@@ -276,6 +346,11 @@ __device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cy
     }
     const bool bad_data = P.check_finite && __any_sync(kFull, fin != fin);
     const bool bad_obj = !(fabsf(cxf) <= 3.402823466e38f) || !(fabsf(cyf) <= 3.402823466e38f);
+    int id0 = 0, id1 = 0;
+    if (P.out_def) {  // warp-uniform; the key bitmap is still intact
+        id0 = slot_id(d0, vo, bm, lane);
+        id1 = slot_id(d1, vo, bm, lane);
+    }
     if (job != nullptr) {
         if (lane == 0) job->cmd = kJobDone;
         named_barrier(kTeamBarJob, kTeamThreads);
@@ -295,9 +370,8 @@ __device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cy
         P.out_status[lp] = status;
         if (P.out_nviol) P.out_nviol[lp] = nviol;
         if (P.out_def) {
-            bool e2 = false;
-            P.out_def[2 * lp] = def_id(d0 - kBoxSlots, vo, e2);
-            P.out_def[2 * lp + 1] = def_id(d1 - kBoxSlots, vo, e2);
+            P.out_def[2 * lp] = id0;
+            P.out_def[2 * lp + 1] = id1;
         }
     }
 }

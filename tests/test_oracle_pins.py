@@ -46,6 +46,23 @@ def test_feistel_is_bijection_on_domain(oracle_mod, m):
         assert sorted(img) == list(range(dom))
 
 
+@pytest.mark.parametrize("m", [3, 17, 300])
+def test_feistel_dec_inverts_enc(oracle_mod, m):
+    dom = 1 << (2 * oracle_mod.half_bits(m))
+    for seed in (1, 77):
+        for x in range(0, dom, max(1, dom // 257)):
+            assert oracle_mod.feistel_dec(seed, m, oracle_mod.feistel_enc(seed, m, x)) == x
+
+
+def test_visit_order_is_increasing_key_order(oracle_mod):
+    # The keys of the visited constraints increase along the order.
+    for m in (2, 9, 100, 1000):
+        for seed in (4, 5):
+            order = oracle_mod.perm_array(seed, m)
+            keys = [oracle_mod.feistel_enc(seed, m, int(q)) for q in order]
+            assert all(a < b for a, b in zip(keys, keys[1:]))
+
+
 def test_perm_is_bijection_and_inverse(oracle_mod):
     sizes = list(range(0, 70)) + [255, 256, 257, 1000, 2047, 2048, 2049, 5000]
     for m in sizes:
