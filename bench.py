@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=20190213)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="time only the FP32 solve (no FP64 comparator, e2e or CPU legs); for profiler captures")
     return ap.parse_args()
 
 
@@ -280,6 +282,18 @@ def run_ours(args):
     # sanity: the timed solves produced a full set of statuses
     st = solver.out_status.cpu().numpy()
     assert ((st >= 0) & (st <= 3)).all()
+
+    if args.kernel_only:
+        if rank == 0:
+            achieved = algo_bytes / (ms * 1e-3) / 1e9
+            print(json.dumps({"metric": METRIC, "value": n_lp * world / (ms_max * 1e-3), "unit": UNIT,
+                              "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+                              "kernel_only": True, "config": {"workload": WORKLOAD, "n_lp": n_lp},
+                              "roofline": {"bound": "hbm", "achieved": achieved}}), flush=True)
+        if pg is not None:
+            pg.barrier()
+            pg.destroy_process_group()
+        return
 
     # ---- FP64 plain uniform solver on the same inputs
     opt64 = lp2d.default_options(precision=lp2d.PREC_FP64, schedule=lp2d.SCHED_UNIFORM)
