@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=20190213)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=1.0,
+                    help="length of the Poisson request stream of the serving leg (0 skips it)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time only the FP32 solve (no FP64 comparator, e2e or CPU legs); for profiler captures")
     return ap.parse_args()
@@ -230,6 +232,7 @@ def run_ours(args):
             pg.barrier()
         torch.cuda.synchronize()
 
+    from paper_1902_04995_gb300 import dist as lpdist
     from paper_1902_04995_gb300 import lp2d, workloads
 
     batch = workloads.ragged(seed=args.seed + rank)
@@ -274,11 +277,7 @@ def run_ours(args):
     barrier()
     sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    ms_max = ms
-    if pg is not None:
-        v = torch.tensor([ms], device=dev)
-        pg.all_reduce(v, op=pg.ReduceOp.MAX)
-        ms_max = float(v.item())
+    ms_max = lpdist.max_over_ranks(ms, device=dev)
     # sanity: the timed solves produced a full set of statuses
     st = solver.out_status.cpu().numpy()
     assert ((st >= 0) & (st <= 3)).all()
@@ -342,17 +341,35 @@ def run_ours(args):
             e2e_step()
         g1.record(stream)
         stream.synchronize()
-    ms_e2e = g0.elapsed_time(g1) / k_e2e
-    if pg is not None:
-        v = torch.tensor([ms_e2e], device=dev)
-        pg.all_reduce(v, op=pg.ReduceOp.MAX)
-        ms_e2e = float(v.item())
+    ms_e2e = lpdist.max_over_ranks(g0.elapsed_time(g1) / k_e2e, device=dev)
 
     if rank != 0:
         if pg is not None:
             pg.barrier()
             pg.destroy_process_group()
         return
+
+    # ---- serving: Poisson requests (2,000/s) admitted under a 20 GB device cap
+    serve_line = None
+    if args.serve_seconds > 0:
+        from paper_1902_04995_gb300 import serve as lpserve
+
+        del solver, s64, dbuf
+        torch.cuda.empty_cache()
+        pool = [lpserve.Payload(workloads.serving_request(args.seed + 17 * i), seed=i) for i in range(6)]
+        arrivals = lpserve.poisson_arrivals(2000.0, args.serve_seconds, seed=args.seed)
+        payloads = [pool[i % len(pool)] for i in range(len(arrivals))]
+        eng = lpserve.ServeEngine(capacity_bytes=20 << 30, n_streams=4, device=dev)
+        for p in pool:  # warm-up: one pass over the pool
+            eng.try_submit(p, 0.0)
+        eng.drain()
+        sstats = eng.run_stream(payloads, arrivals, max_wall_s=60.0 + 5 * args.serve_seconds)
+        serve_line = dict(sstats.summary(), offered_requests_per_s=2000.0, stream_seconds=args.serve_seconds,
+                          request_pool=len(pool), capacity_bytes=20 << 30, streams=4,
+                          mean_lps_per_request=float(np.mean([p.n_lp for p in payloads])) if payloads else 0.0,
+                          mean_constraints_per_request=float(np.mean([p.n_c for p in payloads])) if payloads else 0.0)
+        del eng, pool, payloads
+        torch.cuda.empty_cache()
 
     # ---- CPU baseline: the oracle on the host cores, bounded sample
     cpu = None
@@ -384,6 +401,7 @@ def run_ours(args):
         "e2e": {"value": n_lp * world / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e, "steps": k_e2e},
         "cpu_baseline": cpu,
+        "serve": serve_line,
         "clocks": clocks,
         "gpu_launches": args.steps,
     }

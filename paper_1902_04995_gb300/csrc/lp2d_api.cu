@@ -32,8 +32,7 @@ bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) %
 
 struct DeviceInfo {
     int sms = 0;
-    int occ_f32 = 0;
-    int occ_f64 = 0;
+    int occ[3] = {0, 0, 0};  // resident persistent CTAs per SM, per lp2d_precision
 };
 
 std::mutex g_mu;
@@ -53,11 +52,11 @@ int device_info(DeviceInfo* out) {
     DeviceInfo info;
     e = cudaDeviceGetAttribute(&info.sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "SM count: %s", cudaGetErrorString(e));
-    e = lp2d::persistent_occupancy(false, &info.occ_f32);
-    if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "occupancy (fp32): %s", cudaGetErrorString(e));
-    e = lp2d::persistent_occupancy(true, &info.occ_f64);
-    if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "occupancy (fp64): %s", cudaGetErrorString(e));
-    if (info.occ_f32 < 1 || info.occ_f64 < 1) return fail(LP2D_ERR_CUDA, "persistent kernel cannot be resident");
+    for (int prec = 0; prec < 3; ++prec) {
+        e = lp2d::persistent_occupancy(prec, &info.occ[prec]);
+        if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "occupancy (precision %d): %s", prec, cudaGetErrorString(e));
+        if (info.occ[prec] < 1) return fail(LP2D_ERR_CUDA, "persistent kernel cannot be resident");
+    }
     g_devices[dev] = info;
     *out = info;
     return LP2D_OK;
@@ -131,8 +130,8 @@ int lp2d_solve_batch_ex(const float* ax, const float* ay, const float* b, const 
     if (!finite(box.xmin) || !finite(box.xmax) || !finite(box.ymin) || !finite(box.ymax) ||
         !(box.xmin < box.xmax) || !(box.ymin < box.ymax))
         return fail(LP2D_ERR_INVALID_ARGUMENT, "box must be finite with xmin < xmax and ymin < ymax");
-    if (opt.precision == LP2D_PREC_FP32_F64ISECT)
-        return fail(LP2D_ERR_UNSUPPORTED, "LP2D_PREC_FP32_F64ISECT is not available in this build");
+    if (opt.precision == LP2D_PREC_FP32_F64ISECT && opt.schedule == LP2D_SCHED_UNIFORM)
+        return fail(LP2D_ERR_UNSUPPORTED, "LP2D_PREC_FP32_F64ISECT needs LP2D_SCHED_PERSISTENT");
     if (n_lp == 0) return ok();
     if (!ax || !ay || !b || !offsets || !obj_xy || !out_xy || !out_status)
         return fail(LP2D_ERR_INVALID_ARGUMENT, "NULL data pointer");
@@ -189,14 +188,15 @@ int lp2d_solve_batch_ex(const float* ax, const float* ay, const float* b, const 
         DeviceInfo info;
         int rc = device_info(&info);
         if (rc != LP2D_OK) return rc;
-        const int occ = fp64 ? info.occ_f64 : info.occ_f32;
+        const int occ = info.occ[opt.precision];
         const int per_sm = opt.ctas_per_sm > 0 ? (opt.ctas_per_sm < occ ? opt.ctas_per_sm : occ) : occ;
         long long grid = static_cast<long long>(info.sms) * per_sm;
         const long long useful = (n_lp + lp2d::kPersistentWarps - 1) / lp2d::kPersistentWarps;
         if (grid > useful) grid = useful;
         if (grid < 1) grid = 1;
-        e = fp64 ? lp2d::launch_persistent_f64(p, static_cast<int>(grid), s)
-                 : lp2d::launch_persistent_f32(p, static_cast<int>(grid), s);
+        if (fp64) e = lp2d::launch_persistent_f64(p, static_cast<int>(grid), s);
+        else if (opt.precision == LP2D_PREC_FP32_F64ISECT) e = lp2d::launch_persistent_mixed(p, static_cast<int>(grid), s);
+        else e = lp2d::launch_persistent_f32(p, static_cast<int>(grid), s);
     }
     if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
     return ok();

@@ -74,6 +74,8 @@ struct VisitOrder {
     uint32_t h;      // bits per half
     uint32_t mask;   // (1 << h) - 1
     uint32_t m;      // number of constraints
+    uint32_t up;     // 2^h
+    uint32_t down;   // 2^(32-h)
 
     __device__ __forceinline__ void init_shape(uint32_t m_) {
         m = m_;
@@ -81,6 +83,8 @@ struct VisitOrder {
         h = (bits + 1u) >> 1;
         if (h < 1u) h = 1u;
         mask = (1u << h) - 1u;  // h <= 16 since m < 2^31
+        up = 1u << h;
+        down = 1u << (32u - h);
     }
 
     __device__ __forceinline__ void init(uint64_t seed, uint32_t m_) {
@@ -94,28 +98,31 @@ struct VisitOrder {
     // Size of the key domain, 4^h.
     __device__ __forceinline__ uint64_t domain() const { return 1ull << (2u * h); }
 
+    // Round function: the top h bits of the 32-bit product, taken as the high word of
+    // a second multiply by 2^h; the shifts of this struct are written as multiplies
+    // so that they issue on the multiply-add pipe instead of the integer ALU pipe.
     __device__ __forceinline__ uint32_t f(uint32_t r, uint32_t key) const {
-        return ((r ^ key) * 0x9E3779B1u) >> (32u - h);
+        return __umulhi((r ^ key) * 0x9E3779B1u, up);
     }
 
     // Key of constraint x: four rounds of (L, R) -> (R, L ^ F(R)).
     __device__ __forceinline__ uint32_t enc(uint32_t x) const {
-        uint32_t L = x >> h, R = x & mask, t;
+        uint32_t L = __umulhi(x, down), R = x - L * up, t;
         t = L ^ f(R, k0); L = R; R = t;
         t = L ^ f(R, k1); L = R; R = t;
         t = L ^ f(R, k2); L = R; R = t;
         t = L ^ f(R, k3); L = R; R = t;
-        return (L << h) | R;
+        return L * up + R;
     }
 
     // Constraint with key x: rounds in reverse, (L, R) -> (R ^ F(L), L).
     __device__ __forceinline__ uint32_t dec(uint32_t x) const {
-        uint32_t L = x >> h, R = x & mask, t;
+        uint32_t L = __umulhi(x, down), R = x - L * up, t;
         t = R ^ f(L, k3); R = L; L = t;
         t = R ^ f(L, k2); R = L; L = t;
         t = R ^ f(L, k1); R = L; L = t;
         t = R ^ f(L, k0); R = L; L = t;
-        return (L << h) | R;
+        return L * up + R;
     }
 };
 
@@ -149,6 +156,8 @@ __device__ __forceinline__ void warp_max_pair(int& key, int& pos) {
     pos = __reduce_min_sync(kFull, key == kmax ? pos : kNoPos);
     key = kmax;
 }
+__device__ __forceinline__ int warp_max_key(int key) { return __reduce_max_sync(kFull, key); }
+
 // 64-bit keys: butterfly shuffles.
 __device__ __forceinline__ void warp_min_pair(long long& key, int& pos) {
 #pragma unroll
@@ -165,6 +174,15 @@ __device__ __forceinline__ void warp_max_pair(long long& key, int& pos) {
         int op = __shfl_xor_sync(kFull, pos, off);
         if (ok > key || (ok == key && op < pos)) { key = ok; pos = op; }
     }
+}
+
+__device__ __forceinline__ long long warp_max_key(long long key) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const long long ok = __shfl_xor_sync(kFull, key, off);
+        key = ok > key ? ok : key;
+    }
+    return key;
 }
 
 template <typename Real> struct KeyOf;
@@ -189,6 +207,9 @@ template <> __device__ __forceinline__ float real_div<float>(float a, float b) {
 template <> __device__ __forceinline__ double real_div<double>(double a, double b) { return a / b; }
 
 template <typename Real> __device__ __forceinline__ Real real_abs(Real a) { return a < Real(0) ? -a : a; }
+template <typename Real> __device__ __forceinline__ Real real_max(Real a, Real b);
+template <> __device__ __forceinline__ float real_max<float>(float a, float b) { return fmaxf(a, b); }
+template <> __device__ __forceinline__ double real_max<double>(double a, double b) { return fmax(a, b); }
 
 // Box side s (0..3) as a constraint g.x <= gb, at visit position s - 4:
 //   0: x <= xmax   1: -x <= -xmin   2: y <= ymax   3: -y <= -ymin

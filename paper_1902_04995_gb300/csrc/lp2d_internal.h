@@ -9,6 +9,7 @@ namespace lp2d {
 
 // Shapes of the persistent schedule (see lp2d_persistent.cu).
 constexpr int kPersistentWarps = 4;   // warps per CTA
+constexpr int kPersistentMinCtas = 8; // resident CTAs per SM the FP32 register budget is fitted to
 constexpr int kCapSmall = 508;        // largest LP one warp stages (512 slots with the box)
 constexpr int kCapBig = 2044;         // largest LP a CTA stages (2048 slots with the box)
 constexpr int kMaxChunk = 32;         // LPs per queue grab, at most
@@ -19,12 +20,13 @@ constexpr int kDefaultChunkSmall = 4;
 // Launchers.  Each returns the cudaError_t of the launch.
 cudaError_t launch_persistent_f32(const Params& p, int grid, cudaStream_t s);
 cudaError_t launch_persistent_f64(const Params& p, int grid, cudaStream_t s);
+cudaError_t launch_persistent_mixed(const Params& p, int grid, cudaStream_t s);
 cudaError_t launch_uniform_f32(const Params& p, cudaStream_t s);
 cudaError_t launch_uniform_f64(const Params& p, cudaStream_t s);
 cudaError_t launch_visit_order(uint64_t seed, int64_t m, int64_t* out, cudaStream_t s);
 
 // Resident CTAs per SM of the persistent kernels (occupancy calculator).
-cudaError_t persistent_occupancy(bool fp64, int* ctas_per_sm);
+cudaError_t persistent_occupancy(int precision, int* ctas_per_sm);
 
 // Record a message for lp2d_last_error() on this thread and return `code`.
 int report_error(int code, const char* fmt, ...);

@@ -31,9 +31,8 @@ __device__ __forceinline__ void write_bad(const Params& P, int64_t lp) {
     out[2 * lp] = out[2 * lp + 1] = real_inf<Real>() - real_inf<Real>();
 }
 
-template <typename Real>
-__global__ void __launch_bounds__(kPersistentWarps * 32)
-seidel_persistent_kernel(const Params P) {
+template <typename Real, bool kMixed>
+__device__ __forceinline__ void persistent_body(const Params& P) {
     __shared__ float sX[kStageSlots];
     __shared__ float sY[kStageSlots];
     __shared__ float sB[kStageSlots];
@@ -74,7 +73,7 @@ seidel_persistent_kernel(const Params P) {
             }
             const int m = static_cast<int>(mm);
             if (m > kCapBig) {
-                solve_lp_keys<kPersistentWarps, Real>(P, lp, base, m, &sc, phase, tid);
+                solve_lp_keys<kPersistentWarps, Real, kMixed>(P, lp, base, m, &sc, phase, tid);
                 continue;
             }
             VisitOrder vo;
@@ -84,9 +83,9 @@ seidel_persistent_kernel(const Params P) {
             cp_async_wait_all();
             __syncthreads();
             if (warp == 0)
-                drive_lp<Real>(P, lp, m, s_obj[2 * i], s_obj[2 * i + 1], vo, sX, sY, sB, s_bm, lane, &job);
+                drive_lp<Real, kMixed>(P, lp, m, s_obj[2 * i], s_obj[2 * i + 1], vo, sX, sY, sB, s_bm, lane, &job);
             else
-                team_helper<Real>(sX, sY, sB, &job, tid);
+                team_helper<Real, kMixed>(sX, sY, sB, &job, tid);
             __syncthreads();
         }
     }
@@ -122,7 +121,7 @@ seidel_persistent_kernel(const Params P) {
             stage_lp_warp(vo, m, P.ax + base, P.ay + base, P.b + base, wX, wY, wB, wbm, lane);
             cp_async_wait_all();
             __syncwarp();
-            drive_lp<Real>(P, lp, m, cx, cy, vo, wX, wY, wB, wbm, lane, nullptr);
+            drive_lp<Real, kMixed>(P, lp, m, cx, cy, vo, wX, wY, wB, wbm, lane, nullptr);
             __syncwarp();  // all lanes are done with the stage before it is overwritten
         }
     }
@@ -140,8 +139,26 @@ seidel_persistent_kernel(const Params P) {
     }
 }
 
+// The plain kernels keep the compiler's register choice; the mixed-precision one,
+// whose cold FP64 path would otherwise raise the register count, is fitted to
+// kPersistentMinCtas resident CTAs per SM.
+template <typename Real>
+__global__ void __launch_bounds__(kPersistentWarps * 32) seidel_persistent_kernel(const Params P) {
+    persistent_body<Real, false>(P);
+}
+
+__global__ void __launch_bounds__(kPersistentWarps * 32, kPersistentMinCtas)
+seidel_persistent_mixed_kernel(const Params P) {
+    persistent_body<float, true>(P);
+}
+
 cudaError_t launch_persistent_f32(const Params& p, int grid, cudaStream_t s) {
     seidel_persistent_kernel<float><<<grid, kPersistentWarps * 32, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_persistent_mixed(const Params& p, int grid, cudaStream_t s) {
+    seidel_persistent_mixed_kernel<<<grid, kPersistentWarps * 32, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -150,12 +167,13 @@ cudaError_t launch_persistent_f64(const Params& p, int grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t persistent_occupancy(bool fp64, int* ctas_per_sm) {
-    if (fp64)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, seidel_persistent_kernel<double>,
-                                                             kPersistentWarps * 32, 0);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, seidel_persistent_kernel<float>,
-                                                         kPersistentWarps * 32, 0);
+cudaError_t persistent_occupancy(int precision, int* ctas_per_sm) {
+    const int threads = kPersistentWarps * 32;
+    if (precision == 2)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, seidel_persistent_kernel<double>, threads, 0);
+    if (precision == 1)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, seidel_persistent_mixed_kernel, threads, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, seidel_persistent_kernel<float>, threads, 0);
 }
 
 }  // namespace lp2d

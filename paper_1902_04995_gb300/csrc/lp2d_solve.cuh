@@ -108,7 +108,7 @@ constexpr int64_t kMaxKeyPathM = 1ll << 30;
 // Solve LP `lp` (constraints base .. base+m-1, m <= kMaxKeyPathM) with a team of W
 // warps reading global memory; `tid` is the thread's index within the team.
 // Writes the LP's outputs.
-template <int W, typename Real>
+template <int W, typename Real, bool kMixed = false>
 __device__ void solve_lp_keys(const Params& P, int64_t lp, int64_t base, int m, TeamScratch<W>* sc,
                               unsigned& phase, int tid) {
     constexpr int T = 32 * W;
@@ -173,6 +173,15 @@ __device__ void solve_lp_keys(const Params& P, int64_t lp, int64_t base, int m, 
         const Real sc0 = lb / nrm2;
         const Real p0x = lx * sc0, p0y = ly * sc0;
         const Real ux = -ly, uy = lx;
+        // mixed precision: FP64 foot of the line and the near-parallel threshold
+        double p0x64 = 0.0, p0y64 = 0.0;
+        float lim = 0.0f;
+        if constexpr (kMixed) {
+            const double lx64 = lx, ly64 = ly, sc64 = static_cast<double>(lb) / (lx64 * lx64 + ly64 * ly64);
+            p0x64 = lx64 * sc64;
+            p0y64 = ly64 * sc64;
+            lim = P.tau * P.tau * static_cast<float>(nrm2);
+        }
         Real thi = real_inf<Real>(), tlo = -real_inf<Real>();
         int phi = kNoPos, plo = kNoPos;
         bool par = false;
@@ -192,9 +201,20 @@ __device__ void solve_lp_keys(const Params& P, int64_t lp, int64_t base, int m, 
             const uint32_t g = vo.dec(static_cast<uint32_t>(ek));
             if (g >= static_cast<uint32_t>(m)) continue;
             const Real gx = __ldg(gax + g), gy = __ldg(gay + g), gb = __ldg(gbb + g);
-            const Real den = gx * ux + gy * uy;
-            const Real num = gb - (gx * p0x + gy * p0y);
-            const Real t = real_div<Real>(num, den);
+            Real den = gx * ux + gy * uy;
+            Real num = gb - (gx * p0x + gy * p0y);
+            Real t = real_div<Real>(num, den);
+            if constexpr (kMixed) {
+                if (den * den < lim * (gx * gx + gy * gy)) {  // near-parallel: redo in FP64
+                    const double d64 = (static_cast<double>(gx) * static_cast<double>(ux) +
+                                        static_cast<double>(gy) * static_cast<double>(uy)) + 0.0;
+                    const double n64 = static_cast<double>(gb) -
+                                       (static_cast<double>(gx) * p0x64 + static_cast<double>(gy) * p0y64);
+                    t = static_cast<Real>(n64 / d64);
+                    den = (d64 > 0.0) ? Real(1) : (d64 < 0.0) ? Real(-1) : Real(0);
+                    num = static_cast<Real>(n64);
+                }
+            }
             if (den > Real(0)) {
                 if (t < thi) { thi = t; phi = 4 + ek; }
             } else if (den < Real(0)) {

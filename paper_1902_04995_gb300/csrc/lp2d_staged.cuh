@@ -27,6 +27,8 @@
 namespace lp2d {
 
 constexpr int kBoxSlots = 4;
+constexpr int kScanGroups = 1;  // groups of 32 positions tested per scan step
+constexpr int kWuUnroll = 2;    // unrolling of the 1-D LP loop
 
 __device__ __forceinline__ void cp_async4(float* smem_dst, const float* gsrc) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
@@ -161,38 +163,67 @@ __device__ __forceinline__ int slot_id(int slot, const VisitOrder& vo, const uns
     return static_cast<int>(vo.dec(bitmap_select(bm, nwords, slot - kBoxSlots, lane)));
 }
 
-// One lane's share of a 1-D LP: slots j0, j0 + STRIDE, ... below jend.
-template <typename Real, int STRIDE>
+// One lane's share of a 1-D LP: slots j0, j0 + STRIDE, ... below jend.  The line is
+// p0 + t u with u oriented so that the objective's end is the right end: the right
+// bound (min over den > 0, Eq. 4) is tracked with its slot, the left bound (max over
+// den < 0, Eq. 3) by value only.  den is moved off -0 so that a constraint parallel
+// to the line (den == 0) yields num / +0: -inf when it excludes the line (num < 0),
+// which empties the interval, and +inf or NaN (no effect) when it does not.
+// Mixed-precision data of one 1-D LP: the foot of the line in FP64 and the
+// near-parallel threshold tau^2 |l|^2 (a work unit with den^2 < lim |g|^2 is
+// recomputed in FP64).
+struct MixedLine {
+    double p0x, p0y;
+    float lim;
+};
+
+// kFlag: also report (in *np) whether any work unit had near-parallel normals,
+// |den| < tau |g| |l| (den^2 < lim |g|^2); kMixed: recompute such work units in FP64
+// (the products of the FP32 inputs are exact there).
+template <typename Real, int STRIDE, bool kFlag = false, bool kMixed = false>
 __device__ __forceinline__ void wu_range(const float* __restrict__ sX, const float* __restrict__ sY,
                                          const float* __restrict__ sB, int j0, int jend, Real p0x, Real p0y,
-                                         Real ux, Real uy, Real& thi, int& phi, Real& tlo, int& plo, bool& par) {
-#pragma unroll 2
+                                         Real ux, Real uy, Real& thi, int& phi, Real& tlo,
+                                         const MixedLine& ml = MixedLine{0.0, 0.0, 0.0f}, bool* np = nullptr) {
+    const Real ninf = -real_inf<Real>();
+    bool near = false;
+#pragma unroll kWuUnroll
     for (int j = j0; j < jend; j += STRIDE) {
         const Real gx = sX[j], gy = sY[j], gb = sB[j];
-        const Real den = gx * ux + gy * uy;
+        Real den = (gx * ux + gy * uy) + Real(0);
         const Real num = gb - (gx * p0x + gy * p0y);
-        const Real t = real_div<Real>(num, den);
-        // branch-free: the lanes of a warp see both signs of den
-        const bool pos = den > Real(0);
-        const bool neg = den < Real(0);
-        const bool take_hi = pos && (t < thi);
-        const bool take_lo = neg && (t > tlo);
-        thi = take_hi ? t : thi;
-        phi = take_hi ? j : phi;
-        tlo = take_lo ? t : tlo;
-        plo = take_lo ? j : plo;
-        par = par || (!pos && !neg && num < Real(0));
+        Real t = real_div<Real>(num, den);
+        if constexpr (kFlag || kMixed) {
+            const bool is_near = den * den < ml.lim * (gx * gx + gy * gy);
+            if constexpr (kFlag) near = near || is_near;
+            if constexpr (kMixed) {
+                if (is_near) {
+                    // + 0.0 turns -0 into +0, as for den above: num / +0 is the parallel case
+                    const double d64 = (static_cast<double>(gx) * static_cast<double>(ux) +
+                                        static_cast<double>(gy) * static_cast<double>(uy)) + 0.0;
+                    const double n64 = static_cast<double>(gb) -
+                                       (static_cast<double>(gx) * ml.p0x + static_cast<double>(gy) * ml.p0y);
+                    t = static_cast<Real>(n64 / d64);
+                    den = (d64 < 0.0) ? Real(-1) : Real(1);
+                }
+            }
+        }
+        const bool right = den >= Real(0);
+        const bool take = right && (t < thi);
+        thi = take ? t : thi;
+        phi = take ? j : phi;
+        tlo = real_max<Real>(tlo, right ? ninf : t);
     }
+    if constexpr (kFlag) *np = near;
 }
 
 // Warp-wide reduction of the 1-D LP state; every lane gets the result.
 template <typename Real>
-__device__ __forceinline__ void warp_reduce_1dlp(Real& thi, int& phi, Real& tlo, int& plo, bool& par) {
+__device__ __forceinline__ void warp_reduce_1dlp(Real& thi, int& phi, Real& tlo) {
     using KT = KeyOf<Real>;
     typename KT::type khi = KT::key(thi), klo = KT::key(tlo);
     warp_min_pair(khi, phi);
-    warp_max_pair(klo, plo);
-    par = __any_sync(kFull, par);
+    klo = warp_max_key(klo);
     thi = KT::val(khi);
     tlo = KT::val(klo);
 }
@@ -202,18 +233,19 @@ struct TeamJob {
     int cmd;     // kJobRun or kJobDone
     int fslot;   // slots 0 .. fslot-1 take part
     double p0x, p0y, ux, uy;
+    float lim;  // near-parallel threshold of the mixed-precision mode
     long long khi[4], klo[4];
-    int phi[4], plo[4], par[4];
+    int phi[4];
 };
 constexpr int kJobRun = 1;
 constexpr int kJobDone = 2;
 constexpr int kTeamBarJob = 1;   // named barrier: a job (or done) is posted
 constexpr int kTeamBarPart = 2;  // named barrier: the helpers' partial results are posted
 constexpr int kTeamThreads = 128;
-constexpr int kTeamMinSlots = 384;  // shorter 1-D LPs stay with the driving warp
+constexpr int kTeamMinSlots = 1024;  // shorter 1-D LPs stay with the driving warp
 
 // Helpers (warps 1..3 of the CTA): wait for jobs until the driver posts kJobDone.
-template <typename Real>
+template <typename Real, bool kMixed>
 __device__ void team_helper(const float* __restrict__ sX, const float* __restrict__ sY,
                             const float* __restrict__ sB, TeamJob* job, int tid) {
     const int warp = tid >> 5, lane = tid & 31;
@@ -221,22 +253,19 @@ __device__ void team_helper(const float* __restrict__ sX, const float* __restric
         named_barrier(kTeamBarJob, kTeamThreads);
         if (job->cmd != kJobRun) break;
         Real thi = real_inf<Real>(), tlo = -real_inf<Real>();
-        int phi = kNoPos, plo = kNoPos;
-        bool par = false;
-        wu_range<Real, kTeamThreads>(sX, sY, sB, tid, job->fslot, static_cast<Real>(job->p0x),
-                                     static_cast<Real>(job->p0y), static_cast<Real>(job->ux),
-                                     static_cast<Real>(job->uy), thi, phi, tlo, plo, par);
+        int phi = kNoPos;
+        const MixedLine ml{job->p0x, job->p0y, job->lim};
+        wu_range<Real, kTeamThreads, false, kMixed>(sX, sY, sB, tid, job->fslot, static_cast<Real>(job->p0x),
+                                             static_cast<Real>(job->p0y), static_cast<Real>(job->ux),
+                                             static_cast<Real>(job->uy), thi, phi, tlo, ml);
         using KT = KeyOf<Real>;
         typename KT::type khi = KT::key(thi), klo = KT::key(tlo);
         warp_min_pair(khi, phi);
-        warp_max_pair(klo, plo);
-        par = __any_sync(kFull, par);
+        klo = warp_max_key(klo);
         if (lane == 0) {
             job->khi[warp] = static_cast<long long>(khi);
             job->klo[warp] = static_cast<long long>(klo);
             job->phi[warp] = phi;
-            job->plo[warp] = plo;
-            job->par[warp] = par ? 1 : 0;
         }
         named_barrier(kTeamBarPart, kTeamThreads);
     }
@@ -246,7 +275,7 @@ __device__ void team_helper(const float* __restrict__ sX, const float* __restric
 // (job != nullptr), 1-D LPs over at least kTeamMinSlots slots are shared with the
 // helper warps, and the driver posts kJobDone when it has finished.  Writes the LP's
 // outputs.
-template <typename Real>
+template <typename Real, bool kMixed>
 __device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cyf, const VisitOrder& vo,
                          const float* __restrict__ sX, const float* __restrict__ sY,
                          const float* __restrict__ sB, const unsigned* bm, int lane, TeamJob* job) {
@@ -262,22 +291,31 @@ __device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cy
     float fin = 0.0f;
     int k = 0;
     while (k < m) {
-        const int p = k + lane;
-        bool viol = false;
-        if (p < m) {
-            const float fx = sX[kBoxSlots + p], fy = sY[kBoxSlots + p], fb = sB[kBoxSlots + p];
-            fin = fmaf(fx, 0.0f, fmaf(fy, 0.0f, fmaf(fb, 0.0f, fin)));
-            const Real gx = fx, gy = fy, gb = fb;
-            const Real s = gx * vx + gy * vy - gb;
-            const Real tol = eps * (real_abs(gx) * avx + real_abs(gy) * avy + real_abs(gb));
-            viol = s > tol;
+        // kScanGroups independent groups of 32 positions per step (more work in flight
+        // per dependent step); the first violated position over all groups wins.
+        unsigned bal[kScanGroups];
+#pragma unroll
+        for (int g = 0; g < kScanGroups; ++g) {
+            const int p = k + 32 * g + lane;
+            bool viol = false;
+            if (p < m) {
+                const float fx = sX[kBoxSlots + p], fy = sY[kBoxSlots + p], fb = sB[kBoxSlots + p];
+                fin = fmaf(fx, 0.0f, fmaf(fy, 0.0f, fmaf(fb, 0.0f, fin)));
+                const Real gx = fx, gy = fy, gb = fb;
+                const Real s = gx * vx + gy * vy - gb;
+                const Real tol = eps * (real_abs(gx) * avx + real_abs(gy) * avy + real_abs(gb));
+                viol = s > tol;
+            }
+            bal[g] = __ballot_sync(kFull, viol);
         }
-        const unsigned bal = __ballot_sync(kFull, viol);
-        if (bal == 0u) {
-            k += 32;
+        int first = kNoPos;
+#pragma unroll
+        for (int g = kScanGroups - 1; g >= 0; --g)
+            if (bal[g] != 0u) first = k + 32 * g + __ffs(bal[g]) - 1;
+        if (first == kNoPos) {
+            k += 32 * kScanGroups;
             continue;
         }
-        const int first = k + __ffs(bal) - 1;
         const int fslot = kBoxSlots + first;
         k = first + 1;
         // ---- 1-D LP on the violated line l: lx*x + ly*y = lb
@@ -289,22 +327,33 @@ __device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cy
         }
         const Real sc0 = real_div<Real>(lb, nrm2);
         const Real p0x = lx * sc0, p0y = ly * sc0;  // foot of l
-        const Real ux = -ly, uy = lx;              // direction of l
+        // Direction of l, oriented so that the objective's end is the right end; when
+        // c.u == 0 the left end of u = (-ly, lx) is taken.
+        const Real cu = cx * (-ly) + cy * lx;
+        const Real fs = (cu > Real(0)) ? Real(1) : Real(-1);
+        const Real ux = -ly * fs, uy = lx * fs;
+        MixedLine ml{0.0, 0.0, 0.0f};
+        if constexpr (kMixed) {
+            const double lx64 = lx, ly64 = ly, sc64 = static_cast<double>(lb) / (lx64 * lx64 + ly64 * ly64);
+            ml.p0x = lx64 * sc64;
+            ml.p0y = ly64 * sc64;
+            ml.lim = P.tau * P.tau * static_cast<float>(nrm2);
+        }
         Real thi = real_inf<Real>(), tlo = -real_inf<Real>();
-        int phi = kNoPos, plo = kNoPos;
-        bool par = false;
+        int phi = kNoPos;
         if (job != nullptr && fslot >= kTeamMinSlots) {
             if (lane == 0) {
                 job->cmd = kJobRun;
                 job->fslot = fslot;
-                job->p0x = static_cast<double>(p0x);
-                job->p0y = static_cast<double>(p0y);
+                job->p0x = kMixed ? ml.p0x : static_cast<double>(p0x);
+                job->p0y = kMixed ? ml.p0y : static_cast<double>(p0y);
                 job->ux = static_cast<double>(ux);
                 job->uy = static_cast<double>(uy);
+                job->lim = ml.lim;
             }
             named_barrier(kTeamBarJob, kTeamThreads);
-            wu_range<Real, kTeamThreads>(sX, sY, sB, lane, fslot, p0x, p0y, ux, uy, thi, phi, tlo, plo, par);
-            warp_reduce_1dlp<Real>(thi, phi, tlo, plo, par);
+            wu_range<Real, kTeamThreads, false, kMixed>(sX, sY, sB, lane, fslot, p0x, p0y, ux, uy, thi, phi, tlo, ml);
+            warp_reduce_1dlp<Real>(thi, phi, tlo);
             named_barrier(kTeamBarPart, kTeamThreads);
             using KT = KeyOf<Real>;
             typename KT::type khi = KT::key(thi), klo = KT::key(tlo);
@@ -314,30 +363,50 @@ __device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cy
                 const int ph = job->phi[w];
                 if (kh < khi || (kh == khi && ph < phi)) { khi = kh; phi = ph; }
                 const auto kl = static_cast<typename KT::type>(job->klo[w]);
-                const int pl = job->plo[w];
-                if (kl > klo || (kl == klo && pl < plo)) { klo = kl; plo = pl; }
-                par = par || (job->par[w] != 0);
+                klo = kl > klo ? kl : klo;
             }
             thi = KT::val(khi);
             tlo = KT::val(klo);
         } else {
-            wu_range<Real, 32>(sX, sY, sB, lane, fslot, p0x, p0y, ux, uy, thi, phi, tlo, plo, par);
-            warp_reduce_1dlp<Real>(thi, phi, tlo, plo, par);
+            bool np = false;
+            wu_range<Real, 32, kMixed>(sX, sY, sB, lane, fslot, p0x, p0y, ux, uy, thi, phi, tlo, ml, &np);
+            if (kMixed && __any_sync(kFull, np)) {
+                // a near-parallel pair: redo this 1-D LP with FP64 intersections for them
+                thi = real_inf<Real>();
+                tlo = -real_inf<Real>();
+                phi = kNoPos;
+                wu_range<Real, 32, false, kMixed>(sX, sY, sB, lane, fslot, p0x, p0y, ux, uy, thi, phi, tlo, ml);
+            }
+            warp_reduce_1dlp<Real>(thi, phi, tlo);
         }
         ++nviol;
-        if (par || tlo > thi) {
+        bool empty = !(tlo <= thi);  // an excluding parallel constraint makes thi = -inf
+        Real nvx = p0x + thi * ux, nvy = p0y + thi * uy;
+        if constexpr (kMixed) {
+            // a grazing interval (ends within FP32 rounding of each other): decide the
+            // 1-D LP again in FP64 before trusting emptiness or the endpoint
+            if (!empty && (thi - tlo) <= Real(1e-5) * (real_abs(thi) + real_abs(tlo) + Real(1))) {
+                double th64 = real_inf<double>(), tl64 = -real_inf<double>();
+                int ph64 = kNoPos;
+                wu_range<double, 32>(sX, sY, sB, lane, fslot, ml.p0x, ml.p0y, static_cast<double>(ux),
+                                     static_cast<double>(uy), th64, ph64, tl64);
+                warp_reduce_1dlp<double>(th64, ph64, tl64);
+                empty = !(tl64 <= th64);
+                phi = ph64;
+                nvx = static_cast<Real>(ml.p0x + th64 * static_cast<double>(ux));
+                nvy = static_cast<Real>(ml.p0y + th64 * static_cast<double>(uy));
+            }
+        }
+        if (empty) {
             status = kInfeasible;
             break;
         }
-        const Real cu = cx * ux + cy * uy;
-        const bool right = cu > Real(0);
-        const Real t = right ? thi : tlo;
-        vx = p0x + t * ux;
-        vy = p0y + t * uy;
+        vx = nvx;
+        vy = nvy;
         avx = real_abs(vx);
         avy = real_abs(vy);
         d0 = fslot;
-        d1 = right ? phi : plo;
+        d1 = phi;
     }
     // positions never scanned (the LP stopped early) still take part in the finiteness check
     if (P.check_finite) {

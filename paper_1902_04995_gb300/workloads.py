@@ -218,6 +218,15 @@ def collision(seed=DEFAULT_SEED, n_lp=16384):
     return collision_batch(n_lp, seed=seed)
 
 
+def serving_request(seed, lo_lp=1024, hi_lp=65536, lo_m=16, hi_m=4096):
+    """One serving request: log-uniform [1k, 64k] LPs with sizes log-uniform in
+    [16, 4096], the ragged generator, 10 % infeasible."""
+    rng = np.random.default_rng(seed ^ 0xA11CE)
+    n_lp = int(loguniform_sizes(rng, 1, lo_lp, hi_lp)[0])
+    sizes = loguniform_sizes(rng, n_lp, lo_m, hi_m)
+    return disk_batch(sizes, seed=seed, infeasible_frac=0.1)
+
+
 WORKLOADS = {
     "plain_small_256x64": plain_small,
     "plain_65536x256": plain_at_scale,

@@ -271,3 +271,48 @@ def test_short_form_entry_point():
     torch.cuda.synchronize()
     got = {"xy": xy.cpu().numpy().reshape(-1, 2).astype(np.float64), "status": st.cpu().numpy()}
     assert_parity(batch, got, oracle_solve(batch, seed=0), TOL[lp2d.PREC_FP32])
+
+
+# ------------------------------------------------- precision (near-parallel)
+@pytest.mark.parametrize("prec", [lp2d.PREC_FP32_F64ISECT, lp2d.PREC_FP64])
+def test_collision_workload_mixed_and_fp64(prec):
+    # 16-gon speed limits plus neighbour half-planes, 5 % of them within 1e-6 rad of
+    # an earlier normal: the FP64-intersection and FP64 modes match the oracle.
+    batch = workloads.collision()
+    got = gpu_solve(batch, seed=4, precision=prec)
+    ref = oracle_solve(batch, seed=4)
+    assert_parity(batch, got, ref, TOL[lp2d.PREC_FP32] if prec == lp2d.PREC_FP32_F64ISECT else TOL[prec])
+
+
+def test_mixed_precision_on_plain_and_ragged():
+    for batch in (workloads.plain_at_scale(n_lp=8192), workloads.ragged(n_lp=8192, hi=3000)):
+        got = gpu_solve(batch, seed=6, precision=lp2d.PREC_FP32_F64ISECT)
+        assert_parity(batch, got, oracle_solve(batch, seed=6), TOL[lp2d.PREC_FP32])
+
+
+def test_near_parallel_pair_mixed_mode():
+    # Two constraints whose normals differ by about 1e-7 rad cross far away; the FP32
+    # determinant of such a pair is pure rounding, the mixed mode recomputes it.
+    rng = np.random.default_rng(12)
+    n = 512
+    ang = rng.uniform(0, 2 * np.pi, n)
+    d = np.float32(1e-7)
+    cons = []
+    for a in ang:
+        n1 = np.array([np.cos(a), np.sin(a)], np.float32)
+        n2 = np.array([np.cos(a + d), np.sin(a + d)], np.float32)
+        cons += [[n1[0], n1[1], 1.0], [n2[0], n2[1], 1.0], [-n1[0], -n1[1], 3.0]]
+    cons = np.asarray(cons, np.float32)
+    batch = {"ax": cons[:, 0].copy(), "ay": cons[:, 1].copy(), "b": cons[:, 2].copy(),
+             "offsets": np.arange(0, 3 * n + 1, 3, dtype=np.int64),
+             "obj": np.stack([np.cos(ang + 1.5), np.sin(ang + 1.5)], 1).astype(np.float32), "box": (-1e3, 1e3, -1e3, 1e3)}
+    ref = oracle_solve(batch, seed=2)
+    got = gpu_solve(batch, seed=2, precision=lp2d.PREC_FP32_F64ISECT)
+    assert (got["status"] == ref["status"]).all()
+
+
+def test_mixed_precision_needs_persistent_schedule():
+    batch = workloads.plain_small()
+    with pytest.raises(lp2d.LP2DError) as e:
+        gpu_solve(batch, precision=lp2d.PREC_FP32_F64ISECT, schedule=lp2d.SCHED_UNIFORM)
+    assert e.value.code == lp2d.ERR_UNSUPPORTED
