@@ -244,7 +244,7 @@ constexpr int kTeamBarPart = 2;  // named barrier: the helpers' partial results 
 constexpr int kTeamThreads = 128;
 constexpr int kTeamMinSlots = 1024;  // shorter 1-D LPs stay with the driving warp
 
-// Helpers (warps 1..3 of the CTA): wait for jobs until the driver posts kJobDone.
+// Helpers (the CTA's other three warps): wait for jobs until the driver posts kJobDone.
 template <typename Real, bool kMixed>
 __device__ void team_helper(const float* __restrict__ sX, const float* __restrict__ sY,
                             const float* __restrict__ sB, TeamJob* job, int tid) {
@@ -352,13 +352,17 @@ __device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cy
                 job->lim = ml.lim;
             }
             named_barrier(kTeamBarJob, kTeamThreads);
-            wu_range<Real, kTeamThreads, false, kMixed>(sX, sY, sB, lane, fslot, p0x, p0y, ux, uy, thi, phi, tlo, ml);
+            // the driver takes the slots of its own thread index, like every helper
+            wu_range<Real, kTeamThreads, false, kMixed>(sX, sY, sB, static_cast<int>(threadIdx.x), fslot, p0x, p0y,
+                                                        ux, uy, thi, phi, tlo, ml);
             warp_reduce_1dlp<Real>(thi, phi, tlo);
             named_barrier(kTeamBarPart, kTeamThreads);
             using KT = KeyOf<Real>;
             typename KT::type khi = KT::key(thi), klo = KT::key(tlo);
+            const int self = static_cast<int>(threadIdx.x >> 5);
 #pragma unroll
-            for (int w = 1; w < 4; ++w) {
+            for (int w = 0; w < 4; ++w) {
+                if (w == self) continue;
                 const auto kh = static_cast<typename KT::type>(job->khi[w]);
                 const int ph = job->phi[w];
                 if (kh < khi || (kh == khi && ph < phi)) { khi = kh; phi = ph; }
