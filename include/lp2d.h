@@ -187,6 +187,35 @@ int lp2d_solve_batch_noalloc(const float* ax, const float* ay, const float* b, c
                              int32_t* out_status, const lp2d_options* opt, lp2d_stream_t stream);
 
 /**
+ * Solve a batch whose inputs and outputs live in host memory (pinned memory gives
+ * full copy bandwidth; pageable memory works through staging copies).  The batch
+ * is cut at LP boundaries into chunks that shrink towards the end of the batch
+ * (40, 30, 17, 9 and 4 % of the last 160M constraints, equal chunks of at most 64M
+ * constraints before that; a batch below 2M constraints stays whole).  The chunks
+ * are copied to two library-owned device slots on a library copy stream, so that
+ * copying chunk i+1 overlaps the solve of chunk i on `stream`; the call then costs
+ * about the copy of the whole batch plus the solve of the last, small chunk.  Each
+ * chunk's results are copied back on `stream` right after its solve.
+ *
+ * Arguments are as for lp2d_solve_batch_ex, in host memory: offsets must be host
+ * readable, non-decreasing and >= 0 (checked on the host: LP2D_ERR_INVALID_ARGUMENT
+ * before anything is enqueued).  out_xy is float32[2*n_lp] (float64 for
+ * LP2D_PREC_FP64).  opt->out_nviol / out_def are not supported
+ * (LP2D_ERR_UNSUPPORTED).  Each chunk is solved with seed + (index of its first LP),
+ * so results equal those of one lp2d_solve_batch_ex call over the whole batch.
+ *
+ * On return the work is enqueued.  `stream` is ordered after the last copy-out, so
+ * synchronising `stream` makes the results readable.  The device slots are
+ * allocated on the first call for a (device, stream) pair and grown when a larger
+ * chunk needs them, so such a call must not be inside CUDA-graph capture.  Calls on
+ * one stream share the slots and must not run concurrently from several host
+ * threads.  Returns an lp2d_err.
+ */
+int lp2d_solve_batch_host(const float* ax, const float* ay, const float* b, const int64_t* offsets,
+                          int64_t n_lp, const float* obj_xy, lp2d_box box, void* out_xy,
+                          int32_t* out_status, const lp2d_options* opt, lp2d_stream_t stream);
+
+/**
  * Write the visit order pi of one LP with m constraints and seed seed_l (the seed of
  * LP l is seed + l) into device int64 out[m]: out[k] is the index of the constraint
  * visited at step k.  Runs the same device code the solver uses (Sec. 2.1 asks for a

@@ -4,9 +4,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <utility>
+#include <vector>
 
 #include "lp2d.h"
 #include "lp2d_internal.h"
@@ -253,6 +255,167 @@ int lp2d_read_device_error(void* workspace, lp2d_stream_t stream, uint32_t* out_
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "reading the error word: %s", cudaGetErrorString(e));
     *out_bits = static_cast<uint32_t>(host);
+    return ok();
+}
+
+namespace {
+
+// Library-owned pipeline for lp2d_solve_batch_host, one per (device, caller stream):
+// two device slots (workspace, inputs and outputs of one chunk each), a stream for the
+// host-to-device copies and the events that order them against the solves, which run
+// with their device-to-host copies on the caller's stream.
+struct HostPipe {
+    char* dev = nullptr;
+    size_t slot_bytes = 0;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t in_ready[2] = {nullptr, nullptr};
+    cudaEvent_t solved[2] = {nullptr, nullptr};
+    cudaEvent_t entry = nullptr;  // the caller stream at the start of a call
+};
+
+std::map<std::pair<int, cudaStream_t>, HostPipe> g_pipes;
+
+size_t up256(size_t n) { return (n + 255) / 256 * 256; }
+
+// Bytes of one slot holding the workspace and up to c constraints and n LPs.
+size_t slot_bytes(int64_t c, int64_t n, size_t out_elem) {
+    return up256(4 * c) * 3 + up256(8 * (n + 1)) + up256(8 * n) + up256(2 * out_elem * n) + up256(4 * n) +
+           up256(sizeof(unsigned long long) * lp2d::kWsWords);
+}
+
+}  // namespace
+
+int lp2d_solve_batch_host(const float* ax, const float* ay, const float* b, const int64_t* offsets, int64_t n_lp,
+                          const float* obj_xy, lp2d_box box, void* out_xy, int32_t* out_status,
+                          const lp2d_options* opt_in, lp2d_stream_t stream) {
+    lp2d_options opt;
+    if (opt_in) opt = *opt_in;
+    else lp2d_default_options(&opt);
+    if (opt.out_nviol || opt.out_def)
+        return fail(LP2D_ERR_UNSUPPORTED, "out_nviol / out_def are device outputs; use lp2d_solve_batch_ex");
+    // options, box and n_lp are checked as for a device call, before anything is enqueued
+    lp2d_options ocheck = opt;
+    int rc0 = lp2d_solve_batch_ex(nullptr, nullptr, nullptr, nullptr, n_lp < 0 ? n_lp : 0, nullptr, box, nullptr,
+                                  nullptr, &ocheck, nullptr, 0, stream);
+    if (rc0 != LP2D_OK) return rc0;
+    if (n_lp == 0) return ok();
+    if (!ax || !ay || !b || !offsets || !obj_xy || !out_xy || !out_status)
+        return fail(LP2D_ERR_INVALID_ARGUMENT, "NULL host pointer");
+    for (int64_t l = 0; l < n_lp; ++l)
+        if (offsets[l + 1] < offsets[l])
+            return fail(LP2D_ERR_INVALID_ARGUMENT, "offsets decrease at LP %lld", (long long)l);
+    if (offsets[0] < 0) return fail(LP2D_ERR_INVALID_ARGUMENT, "offsets[0] < 0");
+    const size_t out_elem = (opt.precision == LP2D_PREC_FP64) ? 8 : 4;
+    const int64_t total = offsets[n_lp] - offsets[0];
+
+    // Chunk plan, cut at LP boundaries.  Copies run at the host link's rate and the
+    // solve of a chunk takes about a quarter of its copy time, so the call costs about
+    // the copy of the whole batch plus the solve of the last chunk: chunks shrink
+    // towards the end (40/30/17/9/4 % of the last 160M constraints), and anything
+    // before that goes in equal chunks of at most 64M constraints to bound the slots.
+    // Every split of a copy costs some link throughput, so small batches stay whole.
+    std::vector<int64_t> targets;  // constraint counts from offsets[0] at the cuts
+    constexpr int64_t kWholeBelow = 2 << 20, kTail = 160ll << 20, kHeadChunk = 64ll << 20;
+    if (total >= kWholeBelow) {
+        const int64_t head = total > kTail ? total - kTail : 0;
+        const int64_t nh = (head + kHeadChunk - 1) / kHeadChunk;
+        for (int64_t i = 1; i <= nh; ++i) targets.push_back(head * i / nh);
+        static const int kTailPermille[4] = {400, 700, 870, 960};
+        for (int i = 0; i < 4; ++i) targets.push_back(head + (total - head) * kTailPermille[i] / 1000);
+    }
+    std::vector<int64_t> cut;
+    cut.push_back(0);
+    for (int64_t t : targets) {
+        int64_t c = std::lower_bound(offsets, offsets + n_lp + 1, offsets[0] + t) - offsets;
+        if (c > n_lp) c = n_lp;
+        if (c > cut.back()) cut.push_back(c);
+    }
+    if (cut.back() < n_lp) cut.push_back(n_lp);
+    const int64_t k = static_cast<int64_t>(cut.size()) - 1;
+    int64_t max_c = 0, max_n = 0;
+    for (int64_t i = 0; i < k; ++i) {
+        max_c = std::max(max_c, offsets[cut[i + 1]] - offsets[cut[i]]);
+        max_n = std::max(max_n, cut[i + 1] - cut[i]);
+    }
+    const size_t need = slot_bytes(max_c, max_n, out_elem);
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    const cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    HostPipe* pp = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        HostPipe& p = g_pipes[std::make_pair(dev, cs)];
+        if (!p.copy) {
+            if ((e = cudaStreamCreateWithFlags(&p.copy, cudaStreamNonBlocking)) != cudaSuccess)
+                return fail(LP2D_ERR_CUDA, "copy stream: %s", cudaGetErrorString(e));
+            for (int i = 0; i < 2; ++i) {
+                cudaEventCreateWithFlags(&p.in_ready[i], cudaEventDisableTiming);
+                cudaEventCreateWithFlags(&p.solved[i], cudaEventDisableTiming);
+            }
+            cudaEventCreateWithFlags(&p.entry, cudaEventDisableTiming);
+        }
+        if (p.slot_bytes < need) {
+            // earlier work of this pipeline may still use the old slots
+            if (p.dev) {
+                cudaStreamSynchronize(p.copy);
+                cudaStreamSynchronize(cs);
+                cudaFree(p.dev);
+                p.dev = nullptr;
+                p.slot_bytes = 0;
+            }
+            if ((e = cudaMalloc(&p.dev, 2 * need)) != cudaSuccess)
+                return fail(LP2D_ERR_CUDA, "pipeline buffers (%zu bytes): %s", 2 * need, cudaGetErrorString(e));
+            if ((e = cudaMemset(p.dev, 0, 2 * need)) != cudaSuccess)  // zeroed workspaces
+                return fail(LP2D_ERR_CUDA, "pipeline memset: %s", cudaGetErrorString(e));
+            p.slot_bytes = need;
+        }
+        pp = &p;
+    }
+    HostPipe& p = *pp;
+    // copies of a call start after the caller's earlier work on its stream
+    if ((e = cudaEventRecord(p.entry, cs)) != cudaSuccess || (e = cudaStreamWaitEvent(p.copy, p.entry, 0)) != cudaSuccess)
+        return fail(LP2D_ERR_CUDA, "ordering: %s", cudaGetErrorString(e));
+    for (int64_t i = 0; i < k; ++i) {
+        const int s = static_cast<int>(i & 1);
+        const int64_t lo = cut[i], hi = cut[i + 1], n = hi - lo;
+        if (n == 0) continue;
+        const int64_t c0 = offsets[lo], c = offsets[hi] - c0;
+        // the workspace sits at the start of the slot, at the same place for every call
+        char* dws = p.dev + s * p.slot_bytes;
+        char* base = dws + up256(sizeof(unsigned long long) * lp2d::kWsWords);
+        float* dax = reinterpret_cast<float*>(base);
+        float* day = reinterpret_cast<float*>(base + up256(4 * max_c));
+        float* db = reinterpret_cast<float*>(base + 2 * up256(4 * max_c));
+        int64_t* doff = reinterpret_cast<int64_t*>(base + 3 * up256(4 * max_c));
+        float* dobj = reinterpret_cast<float*>(reinterpret_cast<char*>(doff) + up256(8 * (max_n + 1)));
+        char* dxy = reinterpret_cast<char*>(dobj) + up256(8 * max_n);
+        int32_t* dst = reinterpret_cast<int32_t*>(dxy + up256(2 * out_elem * max_n));
+        // slot s is free once the solve and copy-out of chunk i-2 are done
+        if (i >= 2 && (e = cudaStreamWaitEvent(p.copy, p.solved[s], 0)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(dax, ax + c0, 4 * c, cudaMemcpyHostToDevice, p.copy)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(day, ay + c0, 4 * c, cudaMemcpyHostToDevice, p.copy)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(db, b + c0, 4 * c, cudaMemcpyHostToDevice, p.copy)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(doff, offsets + lo, 8 * (n + 1), cudaMemcpyHostToDevice, p.copy)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(dobj, obj_xy + 2 * lo, 8 * n, cudaMemcpyHostToDevice, p.copy)) != cudaSuccess) break;
+        if ((e = cudaEventRecord(p.in_ready[s], p.copy)) != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(cs, p.in_ready[s], 0)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(dws, 0, sizeof(unsigned long long) * lp2d::kWsWords, cs)) != cudaSuccess) break;
+        // offsets stay absolute: the constraint arrays are passed shifted back by c0
+        lp2d_options oc = opt;
+        oc.seed = opt.seed + static_cast<uint64_t>(lo);
+        const int rc = lp2d_solve_batch_ex(dax - c0, day - c0, db - c0, doff, n, dobj, box, dxy, dst, &oc, dws,
+                                           up256(sizeof(unsigned long long) * lp2d::kWsWords), stream);
+        if (rc != LP2D_OK) return rc;
+        // results (12 bytes per LP) go back on the solve stream, so the copy stream never
+        // waits for a solve except to reuse a slot
+        if ((e = cudaMemcpyAsync(static_cast<char*>(out_xy) + 2 * out_elem * lo, dxy, 2 * out_elem * n,
+                                 cudaMemcpyDeviceToHost, cs)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(out_status + lo, dst, 4 * n, cudaMemcpyDeviceToHost, cs)) != cudaSuccess) break;
+        if ((e = cudaEventRecord(p.solved[s], cs)) != cudaSuccess) break;
+    }
+    if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "host pipeline: %s", cudaGetErrorString(e));
     return ok();
 }
 

@@ -57,7 +57,7 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
         if (tid == 0) s_grab = static_cast<long long>(atomicAdd(ws + kWsHeadBig, static_cast<unsigned long long>(P.chunk_big)));
         __syncthreads();
         const long long start = s_grab;
-        if (start >= P.n_lp) break;
+        if (start < 0 || start >= P.n_lp) break;  // a head past 2^63 is not a valid LP index
         const int cnt = static_cast<int>(min(static_cast<long long>(P.chunk_big), P.n_lp - start));
         if (tid <= cnt) s_off[tid] = __ldg(P.offsets + start + tid);
         if (tid < 2 * cnt) s_obj[tid] = __ldg(P.obj + 2 * start + tid);
@@ -99,7 +99,7 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
         long long start = 0;
         if (lane == 0) start = static_cast<long long>(atomicAdd(ws + kWsHeadSmall, static_cast<unsigned long long>(P.chunk_small)));
         start = __shfl_sync(kFull, start, 0);
-        if (start >= P.n_lp) break;
+        if (start < 0 || start >= P.n_lp) break;
         const int cnt = static_cast<int>(min(static_cast<long long>(P.chunk_small), P.n_lp - start));
         const long long off_l = (lane <= cnt) ? __ldg(P.offsets + start + lane) : 0ll;
         const float obj_l = (lane < 2 * cnt) ? __ldg(P.obj + 2 * start + lane) : 0.0f;

@@ -236,3 +236,46 @@ def solve_batch_noalloc(ax, ay, b, offsets, obj, box, out_xy, out_status, option
     _check(_lib.lp2d_solve_batch_noalloc(_data_ptr(ax), _data_ptr(ay), _data_ptr(b), _ptr(offsets), n_lp,
                                          _data_ptr(obj), Box(*box), _data_ptr(out_xy), _data_ptr(out_status),
                                          ctypes.byref(opts), _stream_handle(stream)))
+
+
+_host_ready = False
+
+
+def _need_host(t, dtype, name, numel=None):
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a host (CPU) tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} has {t.numel()} elements, needs {numel}")
+
+
+def solve_batch_host(ax, ay, b, offsets, obj, box, out_xy, out_status, options: Options | None = None,
+                     stream=None):
+    """lp2d_solve_batch_host: inputs and outputs are host tensors (pinned for full copy
+    bandwidth).  The library copies the batch to the device in chunks, overlapping
+    each chunk's copy with the previous chunk's solve, and copies the results back;
+    synchronise `stream` before reading out_xy / out_status."""
+    global _host_ready
+    if not _host_ready:
+        vp, i64 = ctypes.c_void_p, ctypes.c_int64
+        _lib.lp2d_solve_batch_host.argtypes = [vp, vp, vp, vp, i64, vp, Box, vp, vp, ctypes.POINTER(Options), vp]
+        _lib.lp2d_solve_batch_host.restype = ctypes.c_int
+        _host_ready = True
+    opts = options if options is not None else default_options()
+    out_dtype = torch.float64 if opts.precision == PREC_FP64 else torch.float32
+    n_lp = offsets.numel() - 1
+    if n_lp < 0:
+        raise ValueError("offsets needs n_lp + 1 entries")
+    _need_host(ax, torch.float32, "ax")
+    _need_host(ay, torch.float32, "ay", ax.numel())
+    _need_host(b, torch.float32, "b", ax.numel())
+    _need_host(offsets, torch.int64, "offsets")
+    _need_host(obj, torch.float32, "obj_xy", 2 * n_lp)
+    _need_host(out_xy, out_dtype, "out_xy", 2 * n_lp)
+    _need_host(out_status, torch.int32, "out_status", n_lp)
+    _check(_lib.lp2d_solve_batch_host(_ptr(ax), _ptr(ay), _ptr(b), _ptr(offsets), n_lp, _ptr(obj), Box(*box),
+                                      _ptr(out_xy), _ptr(out_status), ctypes.byref(opts),
+                                      _stream_handle(stream)))

@@ -89,6 +89,47 @@ def test_host_side_validation(lib):
     assert L.lp2d_visit_order(0, 0, None, None) == lib.OK
 
 
+def test_host_entry_validation(lib):
+    import numpy as np
+
+    L = lib._lib
+    B = lib.Box
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    L.lp2d_solve_batch_host.argtypes = [vp, vp, vp, vp, i64, vp, B, vp, vp, ctypes.POINTER(lib.Options), vp]
+    L.lp2d_solve_batch_host.restype = ctypes.c_int
+    box = B(-1, 1, -1, 1)
+    a = np.zeros(8, dtype=np.float32)
+    obj = np.zeros(6, dtype=np.float32)
+    xy = np.zeros(6, dtype=np.float32)
+    st = np.full(3, -5, dtype=np.int32)
+    p = lambda arr: arr.ctypes.data_as(vp)  # noqa: E731
+    # offsets that decrease are rejected on the host before anything is enqueued
+    bad = np.array([0, 4, 2, 8], dtype=np.int64)
+    assert L.lp2d_solve_batch_host(p(a), p(a), p(a), p(bad), 3, p(obj), box, p(xy), p(st), None,
+                                   None) == lib.ERR_INVALID_ARGUMENT
+    assert "decrease" in lib.last_error()
+    assert (st == -5).all()
+    neg = np.array([-1, 4, 6, 8], dtype=np.int64)
+    assert L.lp2d_solve_batch_host(p(a), p(a), p(a), p(neg), 3, p(obj), box, p(xy), p(st), None,
+                                   None) == lib.ERR_INVALID_ARGUMENT
+    # n_lp < 0, bad box, NULL pointers, per-LP diagnostics (device outputs) unsupported
+    good = np.array([0, 4, 6, 8], dtype=np.int64)
+    assert L.lp2d_solve_batch_host(None, None, None, None, -1, None, box, None, None, None,
+                                   None) == lib.ERR_INVALID_ARGUMENT
+    assert L.lp2d_solve_batch_host(p(a), p(a), p(a), p(good), 3, p(obj), B(1, -1, -1, 1), p(xy), p(st), None,
+                                   None) == lib.ERR_INVALID_ARGUMENT
+    assert L.lp2d_solve_batch_host(None, p(a), p(a), p(good), 3, p(obj), box, p(xy), p(st), None,
+                                   None) == lib.ERR_INVALID_ARGUMENT
+    o = lib.default_options(out_nviol=0x1000)
+    assert L.lp2d_solve_batch_host(p(a), p(a), p(a), p(good), 3, p(obj), box, p(xy), p(st), ctypes.byref(o),
+                                   None) == lib.ERR_UNSUPPORTED
+    o = lib.default_options(precision=lib.PREC_FP32_F64ISECT, schedule=lib.SCHED_UNIFORM)
+    assert L.lp2d_solve_batch_host(p(a), p(a), p(a), p(good), 3, p(obj), box, p(xy), p(st), ctypes.byref(o),
+                                   None) == lib.ERR_UNSUPPORTED
+    assert L.lp2d_solve_batch_host(None, None, None, None, 0, None, box, None, None, None, None) == lib.OK
+    assert (st == -5).all()
+
+
 def test_product_path_does_not_import_the_oracle():
     pkg = os.path.join(ROOT, "paper_1902_04995_gb300")
     for dirpath, _, files in os.walk(pkg):
