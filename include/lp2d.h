@@ -66,7 +66,7 @@ typedef enum {
 } lp2d_err;
 
 /** Bits of the device error word kept in the workspace. */
-enum { LP2D_DEVERR_BAD_OFFSETS = 1, LP2D_DEVERR_WALK_LIMIT = 2 };
+enum { LP2D_DEVERR_BAD_OFFSETS = 1 };
 
 /** The bounding box: the +-M constraints of Sec. 2.1 (xmin < xmax, ymin < ymax, finite). */
 typedef struct {

@@ -20,7 +20,7 @@ OPTIMAL, INFEASIBLE, BOX_BOUNDED, BAD_INPUT = 0, 1, 2, 3
 OK, ERR_INVALID_ARGUMENT, ERR_CUDA, ERR_TIMEOUT, ERR_WORKSPACE, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 PREC_FP32, PREC_FP32_F64ISECT, PREC_FP64 = 0, 1, 2
 SCHED_PERSISTENT, SCHED_UNIFORM = 0, 1
-DEVERR_BAD_OFFSETS, DEVERR_WALK_LIMIT = 1, 2
+DEVERR_BAD_OFFSETS = 1
 
 
 class Box(ctypes.Structure):
