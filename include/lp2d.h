@@ -97,8 +97,8 @@ typedef struct {
     int32_t precision;      /**< lp2d_precision; default LP2D_PREC_FP32 */
     int32_t schedule;       /**< lp2d_schedule; default LP2D_SCHED_PERSISTENT */
     int32_t ctas_per_sm;    /**< persistent grid = SMs x this; 0 = occupancy maximum */
-    int32_t chunk_big;      /**< LPs per queue grab by a CTA (1..32); 0 = default 8 */
-    int32_t chunk_small;    /**< LPs per queue grab by a warp (1..16); 0 = default 4 */
+    int32_t chunk_big;      /**< target large LPs per queue grab by a CTA (1..32); 0 = default 1 */
+    int32_t chunk_small;    /**< target LPs per queue grab by a warp (1..16); 0 = default 2 */
     int32_t check_finite;   /**< non-zero: NaN/Inf data gives LP2D_BAD_INPUT; default 1 */
     float eps;              /**< relative violation tolerance; 0 = 1e-6 (FP32) / 1e-12 (FP64) */
     float near_parallel_tau;/**< threshold of LP2D_PREC_FP32_F64ISECT; 0 = 1e-3 */

@@ -27,6 +27,7 @@ constexpr int kWsHeadBig = 0;    // next LP index for CTA teams
 constexpr int kWsHeadSmall = 1;  // next LP index for single warps
 constexpr int kWsDone = 2;       // CTAs that have finished
 constexpr int kWsError = 3;      // device error word
+constexpr int kWsHeadMid = 4;    // next LP index for warps with half a CTA stage
 constexpr int kWsWords = 32;     // 256 bytes
 
 struct Params {

@@ -11,11 +11,12 @@ namespace lp2d {
 constexpr int kPersistentWarps = 4;   // warps per CTA
 constexpr int kPersistentMinCtas = 8; // resident CTAs per SM the FP32 register budget is fitted to
 constexpr int kCapSmall = 508;        // largest LP one warp stages (512 slots with the box)
+constexpr int kCapMid = 1020;         // largest LP one warp stages in half a CTA stage (1024 slots)
 constexpr int kCapBig = 2044;         // largest LP a CTA stages (2048 slots with the box)
-constexpr int kMaxChunk = 32;         // LPs per queue grab, at most
-constexpr int kMaxChunkSmall = 16;    // a warp grab shares its objectives over 32 lanes
-constexpr int kDefaultChunkBig = 8;
-constexpr int kDefaultChunkSmall = 4;
+constexpr int kMaxChunk = 32;         // LP indices per queue grab, at most
+constexpr int kMaxChunkSmall = 16;    // largest target of LPs per warp grab
+constexpr int kDefaultChunkBig = 1;   // target large LPs per CTA grab
+constexpr int kDefaultChunkSmall = 2; // target LPs per warp grab
 
 // Launchers.  Each returns the cudaError_t of the launch.
 cudaError_t launch_persistent_f32(const Params& p, int grid, cudaStream_t s);

@@ -4,11 +4,14 @@
 // threads of a block (Sec. 3).  Here the balancing happens at the level of whole LPs:
 // a grid of (SMs x resident CTAs) persistent CTAs pulls chunks of LP indices from two
 // device queue heads until both are exhausted.
-//   phase 1: LPs with more than kCapWarp constraints, one at a time per CTA: the CTA
+//   phase 1: LPs with more than kCapMid constraints, one at a time per CTA: the CTA
 //            stages the LP in its 24 KB of shared memory, warp 0 runs Seidel's
 //            iterations and warps 1..3 join only the long 1-D LPs (LPs above kCapBig
 //            are read from global memory in visit order instead);
-//   phase 2: LPs with at most kCapWarp constraints, one per warp, each warp with a
+//   phase 2: LPs with more than kCapSmall and at most kCapMid constraints, one per
+//            warp for warps 0 and 1, each with half of the stage (their 1-D LPs are
+//            too short for the helpers, so two drivers share a CTA's stage);
+//   phase 3: LPs with at most kCapSmall constraints, one per warp, each warp with a
 //            quarter of the stage.
 // Large LPs therefore start first and small ones fill the tail.  The last CTA to
 // finish resets the queue heads, so the workspace is ready for the next launch on
@@ -22,6 +25,9 @@ namespace lp2d {
 constexpr int kWarpSlots = kCapSmall + kBoxSlots;                // stage slots per warp
 constexpr int kStageSlots = kPersistentWarps * kWarpSlots;      // stage slots per CTA
 static_assert(kStageSlots - kBoxSlots == kCapBig, "team capacity");
+constexpr int kMidWarps = 2;                                    // warps with half a stage each
+constexpr int kMidSlots = kStageSlots / kMidWarps;              // their stage slots
+static_assert(kMidSlots - kBoxSlots == kCapMid && kMidSlots <= 1024, "half-stage capacity (warp bitmap)");
 
 template <typename Real>
 __device__ __forceinline__ void write_bad(const Params& P, int64_t lp) {
@@ -29,6 +35,33 @@ __device__ __forceinline__ void write_bad(const Params& P, int64_t lp) {
     P.out_status[lp] = kBadInput;
     Real* out = reinterpret_cast<Real*>(P.out_xy);
     out[2 * lp] = out[2 * lp + 1] = real_inf<Real>() - real_inf<Real>();
+}
+
+// Span of the next queue grab: a grab that held none of the caller's LPs doubles it
+// (up to 32), one that held more than `target` of them halves it (down to 1).  A
+// class that is rare in the batch thus costs few queue operations, and a dense one
+// keeps grabs small enough to balance the load across the grid.
+__device__ __forceinline__ int next_span(int span, int found, int target) {
+    if (found == 0) return min(2 * span, 32);
+    if (found > target) return max(span >> 1, 1);
+    return span;
+}
+
+// A warp's next grab from the queue at *head: `span` LP indices starting at the
+// returned index; lane l < span gets the first offset and the size of LP start + l.
+// The caller picks its LPs out of the grab by ballot.
+__device__ __forceinline__ long long warp_grab(const Params& P, unsigned long long* head, int span, int lane,
+                                               long long& off_l, long long& mm_l) {
+    long long start = 0;
+    if (lane == 0) start = static_cast<long long>(atomicAdd(head, static_cast<unsigned long long>(span)));
+    start = __shfl_sync(kFull, start, 0);
+    off_l = 0;
+    mm_l = 0;
+    if (start >= 0 && start < P.n_lp && lane < span && start + lane < P.n_lp) {
+        off_l = __ldg(P.offsets + start + lane);
+        mm_l = __ldg(P.offsets + start + lane + 1) - off_l;
+    }
+    return start;
 }
 
 template <typename Real, bool kMixed>
@@ -51,22 +84,25 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
     unsigned phase = 0;
     unsigned long long* ws = P.ws;
 
-    // ---- phase 1: large LPs, one CTA each
+    // ---- phase 1: large LPs, one CTA each (grab spans adapt as in next_span)
+    int big_span = P.chunk_big;
     for (;;) {
         __syncthreads();  // the previous chunk's s_grab / s_off / stage are no longer read
-        if (tid == 0) s_grab = static_cast<long long>(atomicAdd(ws + kWsHeadBig, static_cast<unsigned long long>(P.chunk_big)));
+        if (tid == 0) s_grab = static_cast<long long>(atomicAdd(ws + kWsHeadBig, static_cast<unsigned long long>(big_span)));
         __syncthreads();
         const long long start = s_grab;
         if (start < 0 || start >= P.n_lp) break;  // a head past 2^63 is not a valid LP index
-        const int cnt = static_cast<int>(min(static_cast<long long>(P.chunk_big), P.n_lp - start));
+        const int cnt = static_cast<int>(min(static_cast<long long>(big_span), P.n_lp - start));
         if (tid <= cnt) s_off[tid] = __ldg(P.offsets + start + tid);
         if (tid < 2 * cnt) s_obj[tid] = __ldg(P.obj + 2 * start + tid);
         __syncthreads();
+        int found = 0;
         for (int i = 0; i < cnt; ++i) {
             const int64_t lp = start + i;
             const int64_t base = s_off[i];
             const int64_t mm = s_off[i + 1] - base;
-            if (mm <= kCapSmall) continue;  // phase 2 (negative sizes are reported there)
+            if (mm <= kCapMid) continue;  // phases 2 and 3 (negative sizes are reported there)
+            ++found;
             if (mm > kMaxKeyPathM) {
                 if (tid == 0) write_bad<Real>(P, lp);
                 continue;
@@ -83,45 +119,79 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
             cp_async_wait_all();
             __syncthreads();
             if (warp == 0)
-                drive_lp<Real, kMixed>(P, lp, m, s_obj[2 * i], s_obj[2 * i + 1], vo, sX, sY, sB, s_bm, lane, &job);
+                drive_lp<Real, kMixed, true>(P, lp, m, s_obj[2 * i], s_obj[2 * i + 1], vo, sX, sY, sB, s_bm, lane, &job);
             else
                 team_helper<Real, kMixed>(sX, sY, sB, &job, tid);
             __syncthreads();
         }
+        big_span = next_span(big_span, found, P.chunk_big);
     }
 
-    // ---- phase 2: small LPs, one warp each
+    // ---- phase 2: mid-size LPs, one warp each for warps 0 and 1 (half a stage each)
+    if (warp < kMidWarps) {
+        float* hX = sX + warp * kMidSlots;
+        float* hY = sY + warp * kMidSlots;
+        float* hB = sB + warp * kMidSlots;
+        unsigned* hbm = s_bm + warp * 32;
+        int span = P.chunk_small;
+        for (;;) {
+            long long off_l, mm_l;
+            const long long start = warp_grab(P, ws + kWsHeadMid, span, lane, off_l, mm_l);
+            if (start < 0 || start >= P.n_lp) break;
+            unsigned todo = __ballot_sync(kFull, lane < span && mm_l > kCapSmall && mm_l <= kCapMid);
+            span = next_span(span, __popc(todo), P.chunk_small);
+            while (todo != 0u) {
+                const int i = __ffs(todo) - 1;
+                todo &= todo - 1u;
+                const int64_t lp = start + i;
+                const int64_t base = __shfl_sync(kFull, off_l, i);
+                const int m = static_cast<int>(__shfl_sync(kFull, mm_l, i));
+                const float cx = __ldg(P.obj + 2 * lp), cy = __ldg(P.obj + 2 * lp + 1);
+                VisitOrder vo;
+                warp_visit_order(vo, P.seed + static_cast<uint64_t>(lp), static_cast<uint32_t>(m), lane);
+                write_box(P, hX, hY, hB, lane);
+                stage_lp_warp(vo, m, P.ax + base, P.ay + base, P.b + base, hX, hY, hB, hbm, lane);
+                cp_async_wait_all();
+                __syncwarp();
+                drive_lp<Real, kMixed, false>(P, lp, m, cx, cy, vo, hX, hY, hB, hbm, lane, nullptr);
+                __syncwarp();  // all lanes are done with the stage before it is overwritten
+            }
+        }
+    }
+    __syncthreads();  // the half stages are free for phase 3
+
+    // ---- phase 3: small LPs, one warp each
     float* wX = sX + warp * kWarpSlots;
     float* wY = sY + warp * kWarpSlots;
     float* wB = sB + warp * kWarpSlots;
     unsigned* wbm = s_bm + warp * 32;
+    int span = P.chunk_small;
     for (;;) {
-        long long start = 0;
-        if (lane == 0) start = static_cast<long long>(atomicAdd(ws + kWsHeadSmall, static_cast<unsigned long long>(P.chunk_small)));
-        start = __shfl_sync(kFull, start, 0);
+        long long off_l, mm_l;
+        const long long start = warp_grab(P, ws + kWsHeadSmall, span, lane, off_l, mm_l);
         if (start < 0 || start >= P.n_lp) break;
-        const int cnt = static_cast<int>(min(static_cast<long long>(P.chunk_small), P.n_lp - start));
-        const long long off_l = (lane <= cnt) ? __ldg(P.offsets + start + lane) : 0ll;
-        const float obj_l = (lane < 2 * cnt) ? __ldg(P.obj + 2 * start + lane) : 0.0f;
-        for (int i = 0; i < cnt; ++i) {
+        // negative sizes (bad offsets) are reported here
+        unsigned todo = __ballot_sync(kFull, lane < span && start + lane < P.n_lp && mm_l <= kCapSmall);
+        span = next_span(span, __popc(todo), P.chunk_small);
+        while (todo != 0u) {
+            const int i = __ffs(todo) - 1;
+            todo &= todo - 1u;
             const int64_t lp = start + i;
             const int64_t base = __shfl_sync(kFull, off_l, i);
-            const int64_t mm = __shfl_sync(kFull, off_l, i + 1) - base;
-            const float cx = __shfl_sync(kFull, obj_l, 2 * i);
-            const float cy = __shfl_sync(kFull, obj_l, 2 * i + 1);
-            if (mm > kCapSmall) continue;
+            const int64_t mm = __shfl_sync(kFull, mm_l, i);
             if (mm < 0) {
                 if (lane == 0) write_bad<Real>(P, lp);
                 continue;
             }
             const int m = static_cast<int>(mm);
+            const float cx = __ldg(P.obj + 2 * lp), cy = __ldg(P.obj + 2 * lp + 1);
             VisitOrder vo;
             warp_visit_order(vo, P.seed + static_cast<uint64_t>(lp), static_cast<uint32_t>(m), lane);
             write_box(P, wX, wY, wB, lane);
             stage_lp_warp(vo, m, P.ax + base, P.ay + base, P.b + base, wX, wY, wB, wbm, lane);
             cp_async_wait_all();
             __syncwarp();
-            drive_lp<Real, kMixed>(P, lp, m, cx, cy, vo, wX, wY, wB, wbm, lane, nullptr);
+            drive_lp<Real, kMixed, false>(P, lp, m, cx, cy, vo, wX, wY, wB, wbm, lane, nullptr);
             __syncwarp();  // all lanes are done with the stage before it is overwritten
         }
     }
@@ -134,6 +204,7 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
         if (prev == static_cast<unsigned long long>(gridDim.x) - 1ull) {
             atomicExch(ws + kWsHeadBig, 0ull);
             atomicExch(ws + kWsHeadSmall, 0ull);
+            atomicExch(ws + kWsHeadMid, 0ull);
             atomicExch(ws + kWsDone, 0ull);
         }
     }

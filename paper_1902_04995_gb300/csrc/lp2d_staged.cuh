@@ -272,10 +272,10 @@ __device__ void team_helper(const float* __restrict__ sX, const float* __restric
 }
 
 // Seidel iterations of one staged LP by one warp (lane = 0..31).  With a team
-// (job != nullptr), 1-D LPs over at least kTeamMinSlots slots are shared with the
-// helper warps, and the driver posts kJobDone when it has finished.  Writes the LP's
-// outputs.
-template <typename Real, bool kMixed>
+// (kTeam, job != nullptr), 1-D LPs over at least kTeamMinSlots slots are shared with
+// the helper warps, and the driver posts kJobDone when it has finished; without one
+// (job unused) the team code is compiled out.  Writes the LP's outputs.
+template <typename Real, bool kMixed, bool kTeam>
 __device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cyf, const VisitOrder& vo,
                          const float* __restrict__ sX, const float* __restrict__ sY,
                          const float* __restrict__ sB, const unsigned* bm, int lane, TeamJob* job) {
@@ -341,7 +341,7 @@ __device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cy
         }
         Real thi = real_inf<Real>(), tlo = -real_inf<Real>();
         int phi = kNoPos;
-        if (job != nullptr && fslot >= kTeamMinSlots) {
+        if (kTeam && fslot >= kTeamMinSlots) {
             if (lane == 0) {
                 job->cmd = kJobRun;
                 job->fslot = fslot;
@@ -424,7 +424,7 @@ __device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cy
         id0 = slot_id(d0, vo, bm, lane);
         id1 = slot_id(d1, vo, bm, lane);
     }
-    if (job != nullptr) {
+    if constexpr (kTeam) {
         if (lane == 0) job->cmd = kJobDone;
         named_barrier(kTeamBarJob, kTeamThreads);
     }
