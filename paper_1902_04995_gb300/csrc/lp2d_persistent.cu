@@ -2,8 +2,8 @@
 //
 // The paper balances the uneven cost of 1-D LPs by spreading work units over the
 // threads of a block (Sec. 3).  Here the balancing happens at the level of whole LPs:
-// a grid of (SMs x resident CTAs) persistent CTAs pulls chunks of LP indices from two
-// device queue heads until both are exhausted.
+// a grid of (SMs x resident CTAs) persistent CTAs pulls spans of LP indices from three
+// device queue heads, one per size class, until all are exhausted.
 //   phase 1: LPs with more than kCapMid constraints, one at a time per CTA: the CTA
 //            stages the LP in its 24 KB of shared memory, warp 0 runs Seidel's
 //            iterations and warps 1..3 join only the long 1-D LPs (LPs above kCapBig
