@@ -27,7 +27,6 @@
 namespace lp2d {
 
 constexpr int kBoxSlots = 4;
-constexpr int kScanGroups = 1;  // groups of 32 positions tested per scan step
 constexpr int kWuUnroll = 2;    // unrolling of the 1-D LP loop
 
 __device__ __forceinline__ void cp_async4(float* smem_dst, const float* gsrc) {
@@ -290,30 +289,46 @@ __device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cy
     int nviol = 0;
     float fin = 0.0f;
     int k = 0;
+    // With a team (large LPs, long violation-free stretches) the values of positions
+    // k + lane are loaded one step ahead of their test, so that the shared-memory
+    // latency leaves the critical path of the scan.
+    float fx = 0.0f, fy = 0.0f, fb = 0.0f;
+    if (kTeam && lane < m) {
+        fx = sX[kBoxSlots + lane];
+        fy = sY[kBoxSlots + lane];
+        fb = sB[kBoxSlots + lane];
+    }
     while (k < m) {
-        // kScanGroups independent groups of 32 positions per step (more work in flight
-        // per dependent step); the first violated position over all groups wins.
-        unsigned bal[kScanGroups];
-#pragma unroll
-        for (int g = 0; g < kScanGroups; ++g) {
-            const int p = k + 32 * g + lane;
-            bool viol = false;
-            if (p < m) {
-                const float fx = sX[kBoxSlots + p], fy = sY[kBoxSlots + p], fb = sB[kBoxSlots + p];
-                fin = fmaf(fx, 0.0f, fmaf(fy, 0.0f, fmaf(fb, 0.0f, fin)));
-                const Real gx = fx, gy = fy, gb = fb;
-                const Real s = gx * vx + gy * vy - gb;
-                const Real tol = eps * (real_abs(gx) * avx + real_abs(gy) * avy + real_abs(gb));
-                viol = s > tol;
+        const int p = k + lane;
+        float nx = 0.0f, ny = 0.0f, nb = 0.0f;
+        if constexpr (kTeam) {
+            if (p + 32 < m) {
+                nx = sX[kBoxSlots + p + 32];
+                ny = sY[kBoxSlots + p + 32];
+                nb = sB[kBoxSlots + p + 32];
             }
-            bal[g] = __ballot_sync(kFull, viol);
+        } else if (p < m) {
+            fx = sX[kBoxSlots + p];
+            fy = sY[kBoxSlots + p];
+            fb = sB[kBoxSlots + p];
         }
-        int first = kNoPos;
-#pragma unroll
-        for (int g = kScanGroups - 1; g >= 0; --g)
-            if (bal[g] != 0u) first = k + 32 * g + __ffs(bal[g]) - 1;
+        bool viol = false;
+        if (p < m) {
+            fin = fmaf(fx, 0.0f, fmaf(fy, 0.0f, fmaf(fb, 0.0f, fin)));
+            const Real gx = fx, gy = fy, gb = fb;
+            const Real s = gx * vx + gy * vy - gb;
+            const Real tol = eps * (real_abs(gx) * avx + real_abs(gy) * avy + real_abs(gb));
+            viol = s > tol;
+        }
+        const unsigned bal = __ballot_sync(kFull, viol);
+        const int first = bal ? k + __ffs(bal) - 1 : kNoPos;
         if (first == kNoPos) {
-            k += 32 * kScanGroups;
+            k += 32;
+            if constexpr (kTeam) {
+                fx = nx;
+                fy = ny;
+                fb = nb;
+            }
             continue;
         }
         const int fslot = kBoxSlots + first;
@@ -411,6 +426,11 @@ __device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cy
         avy = real_abs(vy);
         d0 = fslot;
         d1 = phi;
+        if (kTeam && k + lane < m) {
+            fx = sX[kBoxSlots + k + lane];
+            fy = sY[kBoxSlots + k + lane];
+            fb = sB[kBoxSlots + k + lane];
+        }
     }
     // positions never scanned (the LP stopped early) still take part in the finiteness check
     if (P.check_finite) {

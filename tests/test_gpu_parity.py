@@ -173,6 +173,21 @@ def test_results_identical_across_tuning():
         assert np.array_equal(got["xy"], base["xy"], equal_nan=True), tune
 
 
+@pytest.mark.parametrize("lo,hi,n_lp", [(8, 16, 20000), (509, 1020, 3000), (1021, 2044, 2000), (1, 8, 30000)])
+def test_batches_of_one_size_class(lo, hi, n_lp):
+    # every LP in one size class: the queue of that class is dense and the others are
+    # empty, so each phase's grab spans take their extreme values
+    rng = np.random.default_rng(lo * 7 + hi)
+    sizes = rng.integers(lo, hi + 1, n_lp)
+    batch = workloads.disk_batch(sizes, seed=lo + hi, infeasible_frac=0.1)
+    base = gpu_solve(batch, seed=4)
+    assert_parity(batch, base, oracle_solve(batch, seed=4), TOL[lp2d.PREC_FP32])
+    for tune in ({"chunk_big": 32, "chunk_small": 16}, {"chunk_big": 1, "chunk_small": 1, "ctas_per_sm": 2}):
+        got = gpu_solve(batch, seed=4, **tune)
+        assert (got["status"] == base["status"]).all(), tune
+        assert np.array_equal(got["xy"], base["xy"], equal_nan=True), tune
+
+
 def test_repeated_launches_reuse_workspace_and_graph_replay_is_identical():
     batch = workloads.ragged(n_lp=30000)
     t = to_dev(batch)
