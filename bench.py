@@ -145,13 +145,13 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(inside), "window": window}
 
 
-def oracle_rate(batch, max_seconds: float, min_reps: int = 1):
-    """LPs/s of the FP64 oracle on all host cores, repeating the batch until about
-    max_seconds of CPU work; returns (rate, threads, lps_done, seconds)."""
+def oracle_rate(batch, max_seconds: float, min_reps: int = 1, threads: int | None = None):
+    """LPs/s of the FP64 oracle on `threads` host cores (default: all), repeating the
+    batch until about max_seconds of CPU work; returns (rate, threads, lps_done, seconds)."""
     import oracle
 
     oracle.build()
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     n_lp = len(batch["offsets"]) - 1
     done, t0, reps = 0, time.perf_counter(), 0
     while True:
@@ -397,7 +397,10 @@ def run_ours(args):
     if not args.no_cpu_baseline and world == 1:
         sample = sample_batch(batch, 32768)
         rate, threads, done, el = oracle_rate(sample, max_seconds=8.0)
+        one = sample_batch(batch, 2048)
+        rate1, _, done1, el1 = oracle_rate(one, max_seconds=2.0, threads=1)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "single_thread": {"value": rate1, "unit": UNIT, "sample": f"first 2048 LPs, {done1} LPs in {el1:.1f} s"},
                "sample": f"first 32768 LPs of the {WORKLOAD} workload ({int(sample['offsets'][-1])} constraints), "
                          f"repeated: {done} LPs in {el:.1f} s on {threads} threads"}
 
@@ -413,6 +416,7 @@ def run_ours(args):
                    "l2": "inputs 579 MB > 129 MB L2, no flush", "graph": "one solve per CUDA-graph replay",
                    "parallelism": f"replicas{world}" if world > 1 else "single-gpu", "seed": args.seed},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "frac_of_nominal_8000_gbs": achieved / 8000.0,
                      "peak_kind": f"{peak_kind} copy bandwidth", "traffic": profiled_traffic(WORKLOAD),
                      "kernel": KERNEL},
         "fp64_plain": {"value": n_lp / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
