@@ -5,8 +5,9 @@ import this package.  The product path (``paper_1902_04995_gb300``) never import
 it, and it imports nothing from the product.
 
 The arithmetic lives in ``seidel_oracle.c`` (plain serial Seidel in FP64, Sec. 2.1 of
-the paper, Eqs. 1-4); this module only builds it with gcc and marshals numpy arrays
-through ctypes.  ctypes drops the GIL during a call, so ``threads > 1`` splits a
+the paper, Eqs. 1-4) and ``seidel3_oracle.c`` (the same method in three dimensions,
+the direction Sec. 6 names); this module only builds them with gcc and marshals numpy
+arrays through ctypes.  ctypes drops the GIL during a call, so ``threads > 1`` splits a
 batch by LP range over plain Python threads (one serial solve per LP, no change to
 the arithmetic).
 """
@@ -20,7 +21,7 @@ from concurrent.futures import ThreadPoolExecutor
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "seidel_oracle.c")
+_SRCS = [os.path.join(_HERE, "seidel_oracle.c"), os.path.join(_HERE, "seidel3_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
 OPTIMAL, INFEASIBLE, BOX_BOUNDED, BAD_INPUT = 0, 1, 2, 3
@@ -31,11 +32,12 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile seidel_oracle.c into liboracle.so next to it (portable flags only)."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    """Compile the oracle's C sources into liboracle.so next to them (portable flags only)."""
+    newest = max(os.path.getmtime(f) for f in _SRCS)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, *_SRCS, "-lm"]
         )
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -61,6 +63,8 @@ def _load():
     lib.oracle_solve_batch.restype = None
     lib.oracle_solve_batch.argtypes = [vp, vp, vp, vp, i64, i64, vp, dbl, dbl, dbl, dbl, u64, dbl,
                                        vp, vp, vp, vp]
+    lib.oracle_solve_batch3.restype = None
+    lib.oracle_solve_batch3.argtypes = [vp, vp, vp, vp, vp, i64, i64, vp, vp, u64, dbl, vp, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -141,6 +145,53 @@ def solve_batch(ax, ay, b, offsets, obj, box, seed: int = 0, eps: float = EPS_FP
         with ThreadPoolExecutor(max_workers=threads) as ex:
             list(ex.map(lambda ab: run(*ab), zip(bounds[:-1], bounds[1:])))
     out = {"xy": xy, "status": status}
+    if want_def:
+        out["def"] = dfn
+    if want_nviol:
+        out["nviol"] = nviol
+    return out
+
+
+def _split(offsets, lo, hi, threads):
+    """LP ranges of similar constraint counts for `threads` workers."""
+    csum = offsets[lo:hi + 1] - offsets[lo]
+    cuts = np.searchsorted(csum, np.linspace(0, csum[-1], threads * 8 + 1)[1:-1]) + lo
+    bounds = [lo] + sorted(set(int(c) for c in cuts if lo < c < hi)) + [hi]
+    return list(zip(bounds[:-1], bounds[1:]))
+
+
+def solve_batch3(ax, ay, az, b, offsets, obj, box, seed: int = 0, eps: float = EPS_FP64,
+                 threads: int = 1, want_def: bool = False, want_nviol: bool = False):
+    """Solve every 3-D LP of a CSR batch serially in FP64 (seidel3_oracle.c).
+
+    ax, ay, az, b: float32 [n_constraints]; offsets: int64 [n_lp + 1]; obj: float32
+    [n_lp, 3]; box: (xmin, xmax, ymin, ymax, zmin, zmax).  Returns a dict with ``xyz``
+    (float64 [n_lp, 3]), ``status`` and optionally ``def`` (int32 [n_lp, 3]) and
+    ``nviol`` (violations at the top level, each one a 2-D LP).
+    """
+    lib = _load()
+    arrs = [np.ascontiguousarray(v, dtype=np.float32) for v in (ax, ay, az, b)]
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    obj = np.ascontiguousarray(obj, dtype=np.float32).reshape(-1)
+    n_lp = offsets.shape[0] - 1
+    assert obj.shape[0] == 3 * n_lp
+    box6 = np.asarray([float(np.float32(v)) for v in box], dtype=np.float64)
+    assert box6.shape[0] == 6
+    xyz = np.zeros((n_lp, 3), dtype=np.float64)
+    status = np.zeros(n_lp, dtype=np.int32)
+    dfn = np.zeros((n_lp, 3), dtype=np.int32) if want_def else None
+    nviol = np.zeros(n_lp, dtype=np.int64) if want_nviol else None
+
+    def run(a, z):
+        lib.oracle_solve_batch3(*(_ptr(v) for v in arrs), _ptr(offsets), a, z, _ptr(obj), _ptr(box6),
+                                seed & (2**64 - 1), eps, _ptr(xyz), _ptr(status), _ptr(dfn), _ptr(nviol))
+
+    if threads <= 1 or n_lp < 2 * threads:
+        run(0, n_lp)
+    else:
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(lambda ab: run(*ab), _split(offsets, 0, n_lp, threads)))
+    out = {"xyz": xyz, "status": status}
     if want_def:
         out["def"] = dfn
     if want_nviol:

@@ -28,6 +28,14 @@ Collision-avoidance family (the precision workload):
   ~ U[0, 0.5]; 5 % of neighbour normals are replaced by a copy of an earlier normal
   of the same LP rotated by delta ~ U(-1e-6, 1e-6) rad (near-parallel pairs).  The
   origin is feasible in every LP; the objective is a unit preferred-velocity direction.
+
+Sphere family (the 3-D workloads; constraint i is ax[i] x + ay[i] y + az[i] z <= b[i],
+``obj`` is [n_lp, 3] and ``box`` has six entries):
+  per LP a centre c ~ U[-1,1]^3; per constraint a unit normal n uniform on the sphere
+  (a normalised Gaussian), r ~ U[0.5, 2] and b = r + n.c, so the ball of radius 0.5
+  around c is feasible; the objective is a unit vector uniform on the sphere.  An LP
+  is made infeasible with  -u.x <= -(H + 1),  H = sum of lambda_k b_k over three stored
+  normals with u = sum lambda_k n_k, lambda >= 0 (weak duality bounds u.x by H).
 """
 from __future__ import annotations
 
@@ -227,6 +235,90 @@ def serving_request(seed, lo_lp=1024, hi_lp=65536, lo_m=16, hi_m=4096):
     return disk_batch(sizes, seed=seed, infeasible_frac=0.1)
 
 
+BOX3 = (-BOX_M, BOX_M, -BOX_M, BOX_M, -BOX_M, BOX_M)
+
+
+def _exclusion_plane(rng, n, b):
+    """One plane (a, b) that no point of {n_i . x <= b_i} satisfies (3-D).
+
+    n: [m, 3] stored float32 normals, b: [m] offsets.  Returns float32 values."""
+    n64 = n.astype(np.float64)
+    b64 = b.astype(np.float64)
+    for _ in range(64):
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        near = np.argsort(-(n64 @ u), kind="stable")[:8]
+        for i in range(len(near)):
+            for j in range(i + 1, len(near)):
+                for k in range(j + 1, len(near)):
+                    cone = n64[[near[i], near[j], near[k]]].T
+                    if abs(np.linalg.det(cone)) < 1e-9:
+                        continue
+                    lam = np.linalg.solve(cone, u)
+                    if (lam >= 0.0).all():
+                        h = float(lam @ b64[[near[i], near[j], near[k]]])
+                        return np.float32(-u[0]), np.float32(-u[1]), np.float32(-u[2]), np.float32(-(h + 1.0))
+    raise RuntimeError("no bounded direction found for the exclusion plane")
+
+
+def sphere_batch(sizes, seed=DEFAULT_SEED, infeasible_frac=0.0, box=BOX3):
+    """A batch of 3-D sphere-family LPs with the given constraint counts.
+
+    A fraction ``infeasible_frac`` of the LPs (chosen by a seeded sample among those
+    with at least 8 constraints) gets one appended exclusion plane."""
+    sizes = np.asarray(sizes, dtype=np.int64)
+    rng = np.random.default_rng(seed)
+    n_lp = sizes.shape[0]
+    offsets = np.zeros(n_lp + 1, dtype=np.int64)
+    np.cumsum(sizes, out=offsets[1:])
+    total = int(offsets[-1])
+    centre = rng.uniform(-1.0, 1.0, size=(n_lp, 3))
+    nrm = rng.normal(size=(total, 3))
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    r = rng.uniform(0.5, 2.0, size=total)
+    owner = np.repeat(np.arange(n_lp), sizes)
+    bb = r + np.einsum("ij,ij->i", nrm, centre[owner])
+    obj = rng.normal(size=(n_lp, 3))
+    obj /= np.linalg.norm(obj, axis=1, keepdims=True)
+    n32 = nrm.astype(np.float32)
+    b32 = bb.astype(np.float32)
+    eligible = np.nonzero(sizes >= 8)[0]
+    n_inf = min(int(round(infeasible_frac * n_lp)), eligible.shape[0])
+    infeasible = np.zeros(n_lp, dtype=bool)
+    extra = {}
+    if n_inf > 0:
+        pick = np.sort(eligible[rng.choice(eligible.shape[0], size=n_inf, replace=False)])
+        infeasible[pick] = True
+        for l in pick:
+            s, e = offsets[l], offsets[l + 1]
+            extra[int(l)] = _exclusion_plane(rng, n32[s:e], b32[s:e])
+    new_sizes = sizes + infeasible.astype(np.int64)
+    new_off = np.zeros(n_lp + 1, dtype=np.int64)
+    np.cumsum(new_sizes, out=new_off[1:])
+    dst = np.arange(total, dtype=np.int64) + np.repeat(new_off[:-1] - offsets[:-1], sizes)
+    out = {k: np.empty(int(new_off[-1]), np.float32) for k in ("ax", "ay", "az", "b")}
+    for k, col in (("ax", n32[:, 0]), ("ay", n32[:, 1]), ("az", n32[:, 2]), ("b", b32)):
+        out[k][dst] = col
+    for l, (px, py, pz, pb) in extra.items():
+        slot = new_off[l + 1] - 1
+        out["ax"][slot], out["ay"][slot], out["az"][slot], out["b"][slot] = px, py, pz, pb
+    out.update({"offsets": new_off, "obj": obj.astype(np.float32), "box": tuple(float(v) for v in box),
+                "infeasible": infeasible})
+    return out
+
+
+def plain3d(seed=DEFAULT_SEED, n_lp=65536, m=128):
+    """65,536 3-D LPs x 128 constraints; 10 % get a 129th that makes them infeasible."""
+    return sphere_batch(np.full(n_lp, m, dtype=np.int64), seed=seed, infeasible_frac=0.1)
+
+
+def ragged3d(seed=DEFAULT_SEED, n_lp=65536, lo=8, hi=1020):
+    """65,536 3-D LPs with sizes log-uniform in [8, 1020]; 10 % infeasible."""
+    size_rng = np.random.default_rng(seed ^ 0x3D3D3D)
+    sizes = loguniform_sizes(size_rng, n_lp, lo, hi)
+    return sphere_batch(sizes, seed=seed, infeasible_frac=0.1)
+
+
 WORKLOADS = {
     "plain_small_256x64": plain_small,
     "plain_65536x256": plain_at_scale,
@@ -237,7 +329,10 @@ WORKLOADS = {
 
 def algorithmic_bytes(batch) -> int:
     """Bytes one solve must move at minimum: 12 B per constraint read once, plus per
-    LP 8 B objective, 8 B offset, 8 B result point and 4 B status."""
+    LP 8 B objective, 8 B offset, 8 B result point and 4 B status (3-D: 16 B per
+    constraint and 12 + 8 + 12 + 4 B per LP)."""
     n_c = int(batch["offsets"][-1] - batch["offsets"][0])
     n_lp = int(batch["offsets"].shape[0] - 1)
+    if "az" in batch:
+        return 16 * n_c + 36 * n_lp
     return 12 * n_c + 28 * n_lp
