@@ -1,0 +1,66 @@
+/*
+ * lp3d.h -- C ABI of the batched 3-D linear-program solver.
+ *
+ * The method of Charlton, Maddock & Richmond (arXiv 1902.04995) one dimension up:
+ * the paper gives Seidel's randomized incremental algorithm in two dimensions
+ * (Sec. 2.1) and names higher dimensions as the next step (Sec. 6).  Every LP of a
+ * batch is
+ *
+ *     maximise  c^T x   subject to   A x <= b,   x in R^3
+ *
+ * intersected with a bounding box (six planes).  Constraints are visited in the
+ * same seeded random order as the 2-D solver's (see lp2d_visit_order); when the
+ * current optimum violates the visited constraint, the new optimum is found on that
+ * constraint's plane by a 2-D LP over the box and every earlier constraint, itself
+ * solved by Seidel's 2-D method with 1-D LPs on lines (Eqs. 3, 4).
+ *
+ * Conventions are those of lp2d.h (asynchronous, stream-ordered, caller-owned device
+ * memory, lp2d_last_error() for the reason of a non-zero return), with:
+ * - constraint i: ax[i]*x + ay[i]*y + az[i]*z <= b[i] (float32, SoA); LP l owns
+ *   constraints offsets[l] .. offsets[l+1]-1 (int64 CSR, device);
+ * - obj_xyz[3*l .. 3*l+2] = (c_x, c_y, c_z) of LP l (float32, device);
+ * - out_xyz[3*l .. 3*l+2]: the optimal vertex (float32; float64 for LP2D_PREC_FP64);
+ *   INFEASIBLE and BAD_INPUT LPs get NaN; out_status[l] as in lp2d.h, BOX_BOUNDED when
+ *   a box plane is one of the three planes through the vertex;
+ * - an LP may have at most LP3D_MAX_CONSTRAINTS constraints: a larger one gets status
+ *   LP2D_BAD_INPUT and sets bit LP2D_DEVERR_TOO_LARGE of the workspace error word.
+ */
+#ifndef LP3D_H
+#define LP3D_H
+
+#include "lp2d.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/** Largest LP the 3-D solver stages (1024 stage slots less the six box planes). */
+#define LP3D_MAX_CONSTRAINTS 1018
+
+/** The bounding box (finite, min < max on every axis); the box planes have visit
+ *  positions -6..-1 in the order x <= xmax, -x <= -xmin, y <= ymax, -y <= -ymin,
+ *  z <= zmax, -z <= -zmin, and ids -1..-6 in out_def. */
+typedef struct {
+    float xmin, xmax, ymin, ymax, zmin, zmax;
+} lp3d_box;
+
+/**
+ * Solve a batch of 3-D LPs.  Options as for lp2d_solve_batch_ex: precision
+ * LP2D_PREC_FP32 or LP2D_PREC_FP64 (LP2D_PREC_FP32_F64ISECT and the uniform schedule
+ * give LP2D_ERR_UNSUPPORTED); chunk_small is the target number of LPs per queue grab;
+ * out_nviol counts the violations at the top level (each one a 2-D LP); out_def
+ * receives three constraint ids per LP.  The workspace is lp2d_workspace_bytes()
+ * bytes, zeroed once (lp2d_workspace_init) and reused by later launches on the same
+ * stream; it is not capture-safe to share between concurrent launches.
+ * Returns an lp2d_err.
+ */
+int lp3d_solve_batch_ex(const float* ax, const float* ay, const float* az, const float* b,
+                        const int64_t* offsets, int64_t n_lp, const float* obj_xyz, lp3d_box box,
+                        void* out_xyz, int32_t* out_status, const lp2d_options* opt, void* workspace,
+                        size_t workspace_bytes, lp2d_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LP3D_H */

@@ -279,3 +279,42 @@ def solve_batch_host(ax, ay, b, offsets, obj, box, out_xy, out_status, options: 
     _check(_lib.lp2d_solve_batch_host(_ptr(ax), _ptr(ay), _ptr(b), _ptr(offsets), n_lp, _ptr(obj), Box(*box),
                                       _ptr(out_xy), _ptr(out_status), ctypes.byref(opts),
                                       _stream_handle(stream)))
+
+
+_3d_ready = False
+MAX_CONSTRAINTS_3D = 1018
+DEVERR_TOO_LARGE = 4
+
+
+class Box3(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")]
+
+
+def solve_batch3d(ax, ay, az, b, offsets, obj, box, out_xyz, out_status, options: Options | None = None,
+                  workspace: torch.Tensor | None = None, stream=None):
+    """lp3d_solve_batch_ex: the batched 3-D solver.  obj: float32 [3*n_lp] (device);
+    box: (xmin, xmax, ymin, ymax, zmin, zmax); out_xyz float32 [3*n_lp] (float64 for
+    PREC_FP64); workspace as for solve_batch_ex (see new_workspace)."""
+    global _3d_ready
+    if not _3d_ready:
+        vp, i64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t
+        _lib.lp3d_solve_batch_ex.argtypes = [vp, vp, vp, vp, vp, i64, vp, Box3, vp, vp, ctypes.POINTER(Options), vp,
+                                             sz, vp]
+        _lib.lp3d_solve_batch_ex.restype = ctypes.c_int
+        _3d_ready = True
+    opts = options if options is not None else default_options()
+    out_dtype = torch.float64 if opts.precision == PREC_FP64 else torch.float32
+    n_lp = offsets.numel() - 1
+    if n_lp < 0:
+        raise ValueError("offsets needs n_lp + 1 entries")
+    _need(ax, torch.float32, "ax")
+    for t, name in ((ay, "ay"), (az, "az"), (b, "b")):
+        _need(t, torch.float32, name, ax.numel())
+    _need(offsets, torch.int64, "offsets")
+    _need(obj, torch.float32, "obj_xyz", 3 * n_lp)
+    _need(out_xyz, out_dtype, "out_xyz", 3 * n_lp)
+    _need(out_status, torch.int32, "out_status", n_lp)
+    wbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(_lib.lp3d_solve_batch_ex(_data_ptr(ax), _data_ptr(ay), _data_ptr(az), _data_ptr(b), _ptr(offsets), n_lp,
+                                    _data_ptr(obj), Box3(*box), _data_ptr(out_xyz), _data_ptr(out_status),
+                                    ctypes.byref(opts), _ptr(workspace), wbytes, _stream_handle(stream)))

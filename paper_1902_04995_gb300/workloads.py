@@ -312,8 +312,10 @@ def plain3d(seed=DEFAULT_SEED, n_lp=65536, m=128):
     return sphere_batch(np.full(n_lp, m, dtype=np.int64), seed=seed, infeasible_frac=0.1)
 
 
-def ragged3d(seed=DEFAULT_SEED, n_lp=65536, lo=8, hi=1020):
-    """65,536 3-D LPs with sizes log-uniform in [8, 1020]; 10 % infeasible."""
+def ragged3d(seed=DEFAULT_SEED, n_lp=65536, lo=8, hi=1017):
+    """65,536 3-D LPs with sizes log-uniform in [8, 1017]; 10 % get one more
+    constraint (at most 1018, the 3-D solver's stage capacity) that makes them
+    infeasible."""
     size_rng = np.random.default_rng(seed ^ 0x3D3D3D)
     sizes = loguniform_sizes(size_rng, n_lp, lo, hi)
     return sphere_batch(sizes, seed=seed, infeasible_frac=0.1)

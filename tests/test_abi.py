@@ -9,7 +9,7 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "lp2d.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("lp2d.h", "lp3d.h")]
 
 
 @pytest.fixture(scope="module")
@@ -24,15 +24,15 @@ def lib():
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(lp2d_[a-z_0-9]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(lp[23]d_[a-z_0-9]+)\s*\(", text)))
 
 
 def test_header_declares_the_entry_points():
     names = declared_functions()
     for n in ("lp2d_solve_batch", "lp2d_solve_batch_ex", "lp2d_workspace_bytes", "lp2d_visit_order",
-              "lp2d_last_error", "lp2d_read_device_error"):
+              "lp2d_last_error", "lp2d_read_device_error", "lp3d_solve_batch_ex"):
         assert n in names
 
 
@@ -128,6 +128,27 @@ def test_host_entry_validation(lib):
                                    None) == lib.ERR_UNSUPPORTED
     assert L.lp2d_solve_batch_host(None, None, None, None, 0, None, box, None, None, None, None) == lib.OK
     assert (st == -5).all()
+
+
+def test_3d_host_side_validation(lib):
+    L = lib._lib
+    vp, i64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t
+    L.lp3d_solve_batch_ex.argtypes = [vp, vp, vp, vp, vp, i64, vp, lib.Box3, vp, vp, ctypes.POINTER(lib.Options), vp,
+                                      sz, vp]
+    L.lp3d_solve_batch_ex.restype = ctypes.c_int
+    box = lib.Box3(-1, 1, -1, 1, -1, 1)
+    call = lambda n, b=box, o=None, p=None, ws=None, wsb=0: L.lp3d_solve_batch_ex(  # noqa: E731
+        p, p, p, p, p, n, p, b, p, p, ctypes.byref(o) if o else None, ws, wsb, None)
+    assert call(-1) == lib.ERR_INVALID_ARGUMENT
+    assert call(3, b=lib.Box3(-1, 1, 1, -1, -1, 1)) == lib.ERR_INVALID_ARGUMENT
+    assert call(3, b=lib.Box3(-1, 1, -1, 1, -1, float("inf"))) == lib.ERR_INVALID_ARGUMENT
+    assert call(3, o=lib.default_options(precision=lib.PREC_FP32_F64ISECT)) == lib.ERR_UNSUPPORTED
+    assert call(3, o=lib.default_options(schedule=lib.SCHED_UNIFORM)) == lib.ERR_UNSUPPORTED
+    assert call(0) == lib.OK
+    assert call(3) == lib.ERR_INVALID_ARGUMENT  # NULL data
+    al = ctypes.c_void_p(0x1000)
+    assert call(3, p=al) == lib.ERR_WORKSPACE
+    assert "workspace" in lib.last_error()
 
 
 def test_product_path_does_not_import_the_oracle():

@@ -1,0 +1,144 @@
+"""GPU parity of the batched 3-D solver (lp3d_solve_batch_ex) against the FP64 3-D
+oracle on the same seeded inputs: status bit-exact, the objective within 1e-4
+relative (FP32) or 1e-10 (FP64) of max(|f_oracle|, 1); in FP64 also the number of
+violations and the three defining constraints."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+from paper_1902_04995_gb300 import lp2d, workloads  # noqa: E402
+
+DEV = torch.device("cuda:0")
+THREADS = os.cpu_count() or 1
+TOL = {lp2d.PREC_FP32: 1e-4, lp2d.PREC_FP64: 1e-10}
+
+
+def gpu_solve3(batch, seed=0, precision=lp2d.PREC_FP32, want=False, **tune):
+    t = {k: torch.from_numpy(np.ascontiguousarray(batch[k]).reshape(-1)).to(DEV)
+         for k in ("ax", "ay", "az", "b", "offsets", "obj")}
+    n_lp = len(batch["offsets"]) - 1
+    nviol = torch.full((max(n_lp, 1),), -7, dtype=torch.int32, device=DEV) if want else None
+    dfn = torch.full((max(3 * n_lp, 1),), -7, dtype=torch.int32, device=DEV) if want else None
+    opts = lp2d.default_options(seed=seed, precision=precision, out_nviol=nviol.data_ptr() if want else None,
+                                out_def=dfn.data_ptr() if want else None, **tune)
+    dt = torch.float64 if precision == lp2d.PREC_FP64 else torch.float32
+    xyz = torch.full((max(3 * n_lp, 1),), 12345.0, dtype=dt, device=DEV)
+    st = torch.full((max(n_lp, 1),), -9, dtype=torch.int32, device=DEV)
+    ws = lp2d.new_workspace(n_lp, opts, device=DEV)
+    lp2d.solve_batch3d(t["ax"], t["ay"], t["az"], t["b"], t["offsets"], t["obj"], batch["box"], xyz, st, opts, ws)
+    torch.cuda.synchronize()
+    res = {"xyz": xyz[:3 * n_lp].cpu().numpy().reshape(-1, 3).astype(np.float64), "status": st[:n_lp].cpu().numpy(),
+           "err": lp2d.read_device_error(ws)}
+    if want:
+        res["nviol"] = nviol[:n_lp].cpu().numpy()
+        res["def"] = dfn[:3 * n_lp].cpu().numpy().reshape(-1, 3)
+    return res
+
+
+def oracle3(batch, seed=0, **kw):
+    return oracle.solve_batch3(batch["ax"], batch["ay"], batch["az"], batch["b"], batch["offsets"], batch["obj"],
+                               batch["box"], seed=seed, threads=THREADS, **kw)
+
+
+def assert_parity3(batch, got, ref, tol):
+    bad = np.nonzero(got["status"] != ref["status"])[0]
+    assert bad.size == 0, f"{bad.size} status mismatches, first {bad[:8]}: gpu {got['status'][bad[:8]]} oracle {ref['status'][bad[:8]]}"
+    c = batch["obj"].astype(np.float64)
+    solved = (ref["status"] == oracle.OPTIMAL) | (ref["status"] == oracle.BOX_BOUNDED)
+    f_ref = np.einsum("ij,ij->i", ref["xyz"], c)[solved]
+    f_got = np.einsum("ij,ij->i", got["xyz"], c)[solved]
+    err = np.abs(f_got - f_ref) / np.maximum(np.abs(f_ref), 1.0)
+    assert err.size == 0 or err.max() <= tol, f"max rel objective error {err.max():.3e}"
+    assert np.isnan(got["xyz"][~solved]).all()
+    return err.max(initial=0.0)
+
+
+@pytest.mark.parametrize("prec", [lp2d.PREC_FP32, lp2d.PREC_FP64])
+def test_small_batches_match_the_oracle(prec):
+    for sizes, seed in ((np.full(512, 40), 1), (workloads.loguniform_sizes(np.random.default_rng(5), 3000, 1, 1018), 2)):
+        batch = workloads.sphere_batch(sizes, seed=seed, infeasible_frac=0.1)
+        assert_parity3(batch, gpu_solve3(batch, seed=3, precision=prec), oracle3(batch, seed=3), TOL[prec])
+
+
+def test_fp64_violation_counts_and_defining_planes_match_the_oracle():
+    batch = workloads.sphere_batch(workloads.loguniform_sizes(np.random.default_rng(6), 2000, 1, 1018), seed=4,
+                                   infeasible_frac=0.1)
+    got = gpu_solve3(batch, seed=5, precision=lp2d.PREC_FP64, want=True)
+    ref = oracle3(batch, seed=5, want_def=True, want_nviol=True)
+    assert_parity3(batch, got, ref, TOL[lp2d.PREC_FP64])
+    assert (got["nviol"] == ref["nviol"]).mean() >= 0.999
+    ok = ref["status"] != oracle.INFEASIBLE
+    assert (np.sort(got["def"][ok], 1) == np.sort(ref["def"][ok], 1)).all(1).mean() >= 0.999
+
+
+def test_plain3d_at_scale():
+    batch = workloads.plain3d()
+    got = gpu_solve3(batch, seed=0)
+    assert_parity3(batch, got, oracle3(batch, seed=0), TOL[lp2d.PREC_FP32])
+    assert got["err"] == 0
+
+
+def test_ragged3d_at_scale():
+    batch = workloads.ragged3d()
+    got = gpu_solve3(batch, seed=0)
+    assert_parity3(batch, got, oracle3(batch, seed=0), TOL[lp2d.PREC_FP32])
+
+
+def test_edge_cases_empty_tiny_bad_and_too_large():
+    rng = np.random.default_rng(9)
+    sizes = np.array([0, 1, 2, 3, 6, 31, 32, 33, 505, 506, 507, 1018, 1019, 5000])
+    batch = workloads.sphere_batch(sizes, seed=7)
+    got = gpu_solve3(batch, seed=1)
+    ref = oracle3(batch, seed=1)
+    keep = sizes <= lp2d.MAX_CONSTRAINTS_3D
+    assert (got["status"][~keep] == oracle.BAD_INPUT).all()
+    assert got["err"] & lp2d.DEVERR_TOO_LARGE
+    sub = {k: v for k, v in ref.items()}
+    bad = np.nonzero(got["status"][keep] != ref["status"][keep])[0]
+    assert bad.size == 0, bad
+    c = batch["obj"].astype(np.float64)
+    solved = keep & (ref["status"] != oracle.INFEASIBLE)
+    f_ref = np.einsum("ij,ij->i", ref["xyz"][solved], c[solved])
+    f_got = np.einsum("ij,ij->i", got["xyz"][solved], c[solved])
+    assert (np.abs(f_got - f_ref) / np.maximum(np.abs(f_ref), 1)).max() <= 1e-4
+    # NaN data and a reversed LP (negative size) are BAD_INPUT
+    b2 = workloads.sphere_batch(np.array([10, 10, 10]), seed=8)
+    b2["ax"][12] = np.nan
+    got = gpu_solve3(b2)
+    assert got["status"][1] == oracle.BAD_INPUT and got["status"][0] != oracle.BAD_INPUT
+    b2["offsets"] = np.array([0, 10, 5, 30], np.int64)
+    got = gpu_solve3(b2)
+    assert got["status"][1] == oracle.BAD_INPUT and got["err"] & lp2d.DEVERR_BAD_OFFSETS
+    del sub, rng
+
+
+def test_results_identical_across_tuning_and_repeated_launches():
+    batch = workloads.sphere_batch(workloads.loguniform_sizes(np.random.default_rng(3), 5000, 4, 1018), seed=9,
+                                   infeasible_frac=0.1)
+    base = gpu_solve3(batch, seed=2)
+    for tune in ({"chunk_small": 1}, {"chunk_small": 16, "ctas_per_sm": 1}):
+        got = gpu_solve3(batch, seed=2, **tune)
+        assert (got["status"] == base["status"]).all()
+        assert np.array_equal(got["xyz"], base["xyz"], equal_nan=True)
+    # the workspace is reused without a memset
+    t = {k: torch.from_numpy(np.ascontiguousarray(batch[k]).reshape(-1)).to(DEV)
+         for k in ("ax", "ay", "az", "b", "offsets", "obj")}
+    n = len(batch["offsets"]) - 1
+    opts = lp2d.default_options(seed=2)
+    ws = lp2d.new_workspace(n, opts, device=DEV)
+    xyz = torch.empty(3 * n, device=DEV)
+    st = torch.empty(n, dtype=torch.int32, device=DEV)
+    for _ in range(3):
+        lp2d.solve_batch3d(t["ax"], t["ay"], t["az"], t["b"], t["offsets"], t["obj"], batch["box"], xyz, st, opts, ws)
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == base["status"]).all()
