@@ -59,6 +59,41 @@ int lp3d_solve_batch_ex(const float* ax, const float* ay, const float* az, const
                         void* out_xyz, int32_t* out_status, const lp2d_options* opt, void* workspace,
                         size_t workspace_bytes, lp2d_stream_t stream);
 
+/** Bound of the violation variable of lp2d_least_violation: t <= this factor times
+ *  the largest |box| coordinate. */
+#define LP2D_LEAST_VIOLATION_TMAX_FACTOR 8.0f
+
+/**
+ * Least-violation points of the infeasible LPs of a 2-D batch.  The paper's
+ * application (Sec. 5, collision avoidance) needs a velocity even when an agent's LP
+ * is infeasible, and the paper names, without specifying it, the extra computation
+ * this takes.  This entry point uses the usual choice: the point of the box that
+ * minimises the largest violation,
+ *
+ *     minimise t   subject to   ax[i]*x + ay[i]*y - |(ax[i], ay[i])| t <= b[i],
+ *                               (x, y) in box,  0 <= t <= tmax,
+ *
+ * with tmax = LP2D_LEAST_VIOLATION_TMAX_FACTOR * max |box coordinate| -- a 3-D LP in
+ * (x, y, t) with objective (0, 0, -1), solved by the 3-D solver (so an LP may have at
+ * most LP3D_MAX_CONSTRAINTS constraints).  For a constraint with a unit normal, the
+ * violation is the distance of (x, y) outside it.
+ *
+ * ax, ay, b, offsets, n_lp, box: the 2-D batch as passed to lp2d_solve_batch_ex.
+ * status_in: device int32 [n_lp], the statuses of that solve; only LPs with
+ * LP2D_INFEASIBLE are solved here, the others' outputs are left untouched.
+ * out_xy: device [2*n_lp] (float32; float64 for LP2D_PREC_FP64), the point (x, y) of
+ * each solved LP (it may be the 2-D solve's out_xy, to replace the NaNs there).
+ * out_t: device float32 [n_lp] or NULL, the least violation t.
+ * out_status: device int32 [n_lp], the status of the least-violation LP (OPTIMAL or
+ * BOX_BOUNDED: a box plane, which includes t = 0 and t = tmax, defines the point).
+ * opt: as for lp3d_solve_batch_ex (seed, precision, out_nviol, out_def refer to
+ * the 3-D LP).  Returns an lp2d_err.
+ */
+int lp2d_least_violation(const float* ax, const float* ay, const float* b, const int64_t* offsets,
+                         int64_t n_lp, lp2d_box box, const int32_t* status_in, void* out_xy, float* out_t,
+                         int32_t* out_status, const lp2d_options* opt, void* workspace,
+                         size_t workspace_bytes, lp2d_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

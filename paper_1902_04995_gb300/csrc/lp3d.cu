@@ -56,6 +56,11 @@ struct Params3 {
     double eps64;
     int chunk;
     int check_finite;
+    // least-violation mode: LPs whose status_in is INFEASIBLE, read from 2-D arrays
+    // (az = -|(ax, ay)|, objective (0, 0, -1)); x, y go to out_xyz with a stride of 2
+    // and the violation to out_t
+    const int32_t* __restrict__ status_in;
+    float* out_t;
 };
 
 template <typename Real>
@@ -102,7 +107,7 @@ __device__ __forceinline__ void stage_lp3_warp(const VisitOrder& vo, int m, cons
             const int slot = kBox3 + pe + __popc(we & ((1u << (e & 31u)) - 1u));
             cp_async4(sX + slot, gax + q);
             cp_async4(sY + slot, gay + q);
-            cp_async4(sZ + slot, gaz + q);
+            if (gaz) cp_async4(sZ + slot, gaz + q);
             cp_async4(sB + slot, gb + q);
         }
     }
@@ -124,7 +129,9 @@ __device__ void drive_lp3(const Params3& P, int64_t lp, int m, const VisitOrder&
                           const unsigned* bm, int lane) {
     using KT = KeyOf<Real>;
     using K = typename KT::type;
-    const float cxf = __ldg(P.obj + 3 * lp), cyf = __ldg(P.obj + 3 * lp + 1), czf = __ldg(P.obj + 3 * lp + 2);
+    const bool fallback = P.status_in != nullptr;
+    const float cxf = fallback ? 0.0f : __ldg(P.obj + 3 * lp), cyf = fallback ? 0.0f : __ldg(P.obj + 3 * lp + 1);
+    const float czf = fallback ? -1.0f : __ldg(P.obj + 3 * lp + 2);
     const Real cx = cxf, cy = cyf, cz = czf;
     const Real eps = (sizeof(Real) == 4) ? Real(P.eps32) : Real(P.eps64);
     Real vx = cx >= Real(0) ? Real(P.box[1]) : Real(P.box[0]);
@@ -297,13 +304,16 @@ __device__ void drive_lp3(const Params3& P, int64_t lp, int m, const VisitOrder&
         if (bad_data || bad_obj) status = kBadInput;
         else if (status < 0) status = (d0 < kBox3 || d1 < kBox3 || d2 < kBox3) ? kBoxBounded : kOptimal;
         Real* out = reinterpret_cast<Real*>(P.out_xyz);
-        if (status == kInfeasible || status == kBadInput) {
-            const Real nan = real_inf<Real>() - real_inf<Real>();
-            out[3 * lp] = out[3 * lp + 1] = out[3 * lp + 2] = nan;
+        const bool none = status == kInfeasible || status == kBadInput;
+        const Real nan = real_inf<Real>() - real_inf<Real>();
+        if (fallback) {
+            out[2 * lp] = none ? nan : vx;
+            out[2 * lp + 1] = none ? nan : vy;
+            if (P.out_t) P.out_t[lp] = none ? nan : static_cast<float>(vz);
         } else {
-            out[3 * lp] = vx;
-            out[3 * lp + 1] = vy;
-            out[3 * lp + 2] = vz;
+            out[3 * lp] = none ? nan : vx;
+            out[3 * lp + 1] = none ? nan : vy;
+            out[3 * lp + 2] = none ? nan : vz;
         }
         P.out_status[lp] = status;
         if (P.out_nviol) P.out_nviol[lp] = nviol;
@@ -320,7 +330,13 @@ __device__ __forceinline__ void write_bad3(const Params3& P, int64_t lp, unsigne
     atomicOr(P.ws + kWsError, static_cast<unsigned long long>(bits));
     P.out_status[lp] = kBadInput;
     Real* out = reinterpret_cast<Real*>(P.out_xyz);
-    out[3 * lp] = out[3 * lp + 1] = out[3 * lp + 2] = real_inf<Real>() - real_inf<Real>();
+    const Real nan = real_inf<Real>() - real_inf<Real>();
+    if (P.status_in != nullptr) {
+        out[2 * lp] = out[2 * lp + 1] = nan;
+        if (P.out_t) P.out_t[lp] = nan;
+    } else {
+        out[3 * lp] = out[3 * lp + 1] = out[3 * lp + 2] = nan;
+    }
 }
 
 // One warp's loop over a queue: grab spans of LP indices (doubling after a grab
@@ -341,7 +357,8 @@ __device__ void warp_queue3(const Params3& P, unsigned long long* head, long lon
             off_l = __ldg(P.offsets + start + lane);
             mm_l = __ldg(P.offsets + start + lane + 1) - off_l;
         }
-        unsigned todo = __ballot_sync(kFull, in && mm_l > lo && mm_l <= hi);
+        const bool wanted = P.status_in == nullptr || (in && __ldg(P.status_in + start + lane) == kInfeasible);
+        unsigned todo = __ballot_sync(kFull, in && wanted && mm_l > lo && mm_l <= hi);
         const int found = __popc(todo);
         span = found == 0 ? min(2 * span, 32) : (found > P.chunk ? max(span >> 1, 1) : span);
         while (todo != 0u) {
@@ -358,9 +375,19 @@ __device__ void warp_queue3(const Params3& P, unsigned long long* head, long lon
             VisitOrder vo;
             warp_visit_order(vo, P.seed + static_cast<uint64_t>(lp), static_cast<uint32_t>(m), lane);
             write_box3(P, sX, sY, sZ, sB, lane);
-            stage_lp3_warp(vo, m, P.ax + base, P.ay + base, P.az + base, P.b + base, sX, sY, sZ, sB, bm, lane);
+            stage_lp3_warp(vo, m, P.ax + base, P.ay + base, P.az ? P.az + base : nullptr, P.b + base, sX, sY, sZ,
+                           sB, bm, lane);
             cp_async_wait_all();
             __syncwarp();
+            if (P.az == nullptr) {
+                // least violation: the third coefficient is -|(ax, ay)| (each product and
+                // the sum rounded separately, so that it equals the plain float32 value)
+                for (int i = lane; i < m; i += 32) {
+                    const int sl = kBox3 + i;
+                    sZ[sl] = -sqrtf(__fadd_rn(__fmul_rn(sX[sl], sX[sl]), __fmul_rn(sY[sl], sY[sl])));
+                }
+                __syncwarp();
+            }
             drive_lp3<Real>(P, lp, m, vo, sX, sY, sZ, sB, bm, lane);
             __syncwarp();  // all lanes are done with the stage before it is overwritten
         }
@@ -419,6 +446,52 @@ int occupancy3(bool fp64, int* sms, int* per_sm) {
 
 }  // namespace
 
+namespace {
+
+int launch3(lp2d::Params3& p, const lp2d_options& opt, int64_t n_lp, lp2d_stream_t stream) {
+    using lp2d::report_error;
+    const bool fp64 = opt.precision == LP2D_PREC_FP64;
+    int sms = 0, per_sm = 0;
+    int rc = occupancy3(fp64, &sms, &per_sm);
+    if (rc != LP2D_OK) return rc;
+    if (opt.ctas_per_sm > 0 && opt.ctas_per_sm < per_sm) per_sm = opt.ctas_per_sm;
+    long long grid = static_cast<long long>(sms) * per_sm;
+    const long long useful = (n_lp + lp2d::kWarps3 - 1) / lp2d::kWarps3;
+    if (grid > useful) grid = useful;
+    if (grid < 1) grid = 1;
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (fp64) lp2d::seidel3_kernel<double><<<static_cast<int>(grid), lp2d::kWarps3 * 32, 0, s>>>(p);
+    else lp2d::seidel3_kernel<float><<<static_cast<int>(grid), lp2d::kWarps3 * 32, 0, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return report_error(LP2D_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return LP2D_OK;
+}
+
+int check_options3(const lp2d_options& opt) {
+    using lp2d::report_error;
+    if (opt.precision != LP2D_PREC_FP32 && opt.precision != LP2D_PREC_FP64)
+        return report_error(LP2D_ERR_UNSUPPORTED, "the 3-D solver runs in FP32 or FP64");
+    if (opt.schedule != LP2D_SCHED_PERSISTENT)
+        return report_error(LP2D_ERR_UNSUPPORTED, "the 3-D solver has the persistent schedule only");
+    if (opt.chunk_small < 0 || !(opt.eps >= 0.0f) || !std::isfinite(opt.eps))
+        return report_error(LP2D_ERR_INVALID_ARGUMENT, "bad tuning parameter or eps");
+    return LP2D_OK;
+}
+
+void fill_common3(lp2d::Params3& p, const lp2d_options& opt, void* workspace) {
+    p.seed = opt.seed;
+    p.out_nviol = opt.out_nviol;
+    p.out_def = opt.out_def;
+    p.ws = reinterpret_cast<unsigned long long*>(workspace);
+    p.eps32 = opt.eps > 0.0f ? opt.eps : 1e-6f;
+    p.eps64 = opt.eps > 0.0f ? static_cast<double>(opt.eps) : 1e-12;
+    p.chunk = opt.chunk_small > 0 ? (opt.chunk_small < lp2d::kMaxChunkSmall ? opt.chunk_small : lp2d::kMaxChunkSmall)
+                                  : lp2d::kDefaultChunkSmall;
+    p.check_finite = opt.check_finite ? 1 : 0;
+}
+
+}  // namespace
+
 extern "C" {
 
 int lp3d_solve_batch_ex(const float* ax, const float* ay, const float* az, const float* b, const int64_t* offsets,
@@ -429,12 +502,8 @@ int lp3d_solve_batch_ex(const float* ax, const float* ay, const float* az, const
     if (opt_in) opt = *opt_in;
     else lp2d_default_options(&opt);
     if (n_lp < 0) return report_error(LP2D_ERR_INVALID_ARGUMENT, "n_lp = %lld < 0", (long long)n_lp);
-    if (opt.precision != LP2D_PREC_FP32 && opt.precision != LP2D_PREC_FP64)
-        return report_error(LP2D_ERR_UNSUPPORTED, "the 3-D solver runs in FP32 or FP64");
-    if (opt.schedule != LP2D_SCHED_PERSISTENT)
-        return report_error(LP2D_ERR_UNSUPPORTED, "the 3-D solver has the persistent schedule only");
-    if (opt.chunk_small < 0 || !(opt.eps >= 0.0f) || !std::isfinite(opt.eps))
-        return report_error(LP2D_ERR_INVALID_ARGUMENT, "bad tuning parameter or eps");
+    int rc0 = check_options3(opt);
+    if (rc0 != LP2D_OK) return rc0;
     const float bx[6] = {box.xmin, box.xmax, box.ymin, box.ymax, box.zmin, box.zmax};
     for (int i = 0; i < 6; ++i)
         if (!std::isfinite(bx[i])) return report_error(LP2D_ERR_INVALID_ARGUMENT, "box must be finite");
@@ -462,33 +531,59 @@ int lp3d_solve_batch_ex(const float* ax, const float* ay, const float* az, const
     p.n_lp = n_lp;
     p.obj = obj_xyz;
     for (int i = 0; i < 6; ++i) p.box[i] = bx[i];
-    p.seed = opt.seed;
     p.out_xyz = out_xyz;
     p.out_status = out_status;
-    p.out_nviol = opt.out_nviol;
-    p.out_def = opt.out_def;
-    p.ws = reinterpret_cast<unsigned long long*>(workspace);
-    p.eps32 = opt.eps > 0.0f ? opt.eps : 1e-6f;
-    p.eps64 = opt.eps > 0.0f ? static_cast<double>(opt.eps) : 1e-12;
-    p.chunk = opt.chunk_small > 0 ? (opt.chunk_small < lp2d::kMaxChunkSmall ? opt.chunk_small : lp2d::kMaxChunkSmall)
-                                  : lp2d::kDefaultChunkSmall;
-    p.check_finite = opt.check_finite ? 1 : 0;
+    fill_common3(p, opt, workspace);
+    return launch3(p, opt, n_lp, stream);
+}
 
-    const bool fp64 = opt.precision == LP2D_PREC_FP64;
-    int sms = 0, per_sm = 0;
-    int rc = occupancy3(fp64, &sms, &per_sm);
-    if (rc != LP2D_OK) return rc;
-    if (opt.ctas_per_sm > 0 && opt.ctas_per_sm < per_sm) per_sm = opt.ctas_per_sm;
-    long long grid = static_cast<long long>(sms) * per_sm;
-    const long long useful = (n_lp + lp2d::kWarps3 - 1) / lp2d::kWarps3;
-    if (grid > useful) grid = useful;
-    if (grid < 1) grid = 1;
-    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (fp64) lp2d::seidel3_kernel<double><<<static_cast<int>(grid), lp2d::kWarps3 * 32, 0, s>>>(p);
-    else lp2d::seidel3_kernel<float><<<static_cast<int>(grid), lp2d::kWarps3 * 32, 0, s>>>(p);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return report_error(LP2D_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
-    return LP2D_OK;
+int lp2d_least_violation(const float* ax, const float* ay, const float* b, const int64_t* offsets, int64_t n_lp,
+                         lp2d_box box, const int32_t* status_in, void* out_xy, float* out_t, int32_t* out_status,
+                         const lp2d_options* opt_in, void* workspace, size_t workspace_bytes, lp2d_stream_t stream) {
+    using lp2d::report_error;
+    lp2d_options opt;
+    if (opt_in) opt = *opt_in;
+    else lp2d_default_options(&opt);
+    if (n_lp < 0) return report_error(LP2D_ERR_INVALID_ARGUMENT, "n_lp = %lld < 0", (long long)n_lp);
+    int rc0 = check_options3(opt);
+    if (rc0 != LP2D_OK) return rc0;
+    if (!std::isfinite(box.xmin) || !std::isfinite(box.xmax) || !std::isfinite(box.ymin) ||
+        !std::isfinite(box.ymax) || !(box.xmin < box.xmax) || !(box.ymin < box.ymax))
+        return report_error(LP2D_ERR_INVALID_ARGUMENT, "box must be finite with xmin < xmax and ymin < ymax");
+    if (n_lp == 0) return LP2D_OK;
+    if (!ax || !ay || !b || !offsets || !status_in || !out_xy || !out_status)
+        return report_error(LP2D_ERR_INVALID_ARGUMENT, "NULL data pointer");
+    const size_t out_align = (opt.precision == LP2D_PREC_FP64) ? 8 : 4;
+    if (!aligned3(ax, 4) || !aligned3(ay, 4) || !aligned3(b, 4) || !aligned3(offsets, 8) ||
+        !aligned3(status_in, 4) || !aligned3(out_xy, out_align) || (out_t && !aligned3(out_t, 4)) ||
+        !aligned3(out_status, 4) || (opt.out_nviol && !aligned3(opt.out_nviol, 4)) ||
+        (opt.out_def && !aligned3(opt.out_def, 4)))
+        return report_error(LP2D_ERR_INVALID_ARGUMENT, "misaligned pointer");
+    const size_t need = sizeof(unsigned long long) * lp2d::kWsWords;
+    if (!workspace) return report_error(LP2D_ERR_WORKSPACE, "workspace is NULL (need %zu bytes)", need);
+    if (workspace_bytes < need || !aligned3(workspace, 8))
+        return report_error(LP2D_ERR_WORKSPACE, "workspace needs %zu bytes, 8-byte aligned", need);
+    const float bm = fmaxf(fmaxf(fabsf(box.xmin), fabsf(box.xmax)), fmaxf(fabsf(box.ymin), fabsf(box.ymax)));
+    lp2d::Params3 p{};
+    p.ax = ax;
+    p.ay = ay;
+    p.az = nullptr;
+    p.b = b;
+    p.offsets = offsets;
+    p.n_lp = n_lp;
+    p.obj = nullptr;
+    p.box[0] = box.xmin;
+    p.box[1] = box.xmax;
+    p.box[2] = box.ymin;
+    p.box[3] = box.ymax;
+    p.box[4] = 0.0f;
+    p.box[5] = LP2D_LEAST_VIOLATION_TMAX_FACTOR * bm;
+    p.out_xyz = out_xy;
+    p.out_status = out_status;
+    p.status_in = status_in;
+    p.out_t = out_t;
+    fill_common3(p, opt, workspace);
+    return launch3(p, opt, n_lp, stream);
 }
 
 }  // extern "C"

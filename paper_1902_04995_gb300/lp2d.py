@@ -318,3 +318,37 @@ def solve_batch3d(ax, ay, az, b, offsets, obj, box, out_xyz, out_status, options
     _check(_lib.lp3d_solve_batch_ex(_data_ptr(ax), _data_ptr(ay), _data_ptr(az), _data_ptr(b), _ptr(offsets), n_lp,
                                     _data_ptr(obj), Box3(*box), _data_ptr(out_xyz), _data_ptr(out_status),
                                     ctypes.byref(opts), _ptr(workspace), wbytes, _stream_handle(stream)))
+
+
+_lv_ready = False
+LEAST_VIOLATION_TMAX_FACTOR = 8.0
+
+
+def least_violation(ax, ay, b, offsets, box, status_in, out_xy, out_status, out_t=None,
+                    options: Options | None = None, workspace: torch.Tensor | None = None, stream=None):
+    """lp2d_least_violation: for every LP whose status_in is INFEASIBLE, the point of
+    the box with the smallest largest violation (a 3-D LP in (x, y, t)); writes
+    out_xy (2 per LP), out_status and, if given, out_t.  Other LPs are untouched."""
+    global _lv_ready
+    if not _lv_ready:
+        vp, i64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t
+        _lib.lp2d_least_violation.argtypes = [vp, vp, vp, vp, i64, Box, vp, vp, vp, vp, ctypes.POINTER(Options), vp,
+                                              sz, vp]
+        _lib.lp2d_least_violation.restype = ctypes.c_int
+        _lv_ready = True
+    opts = options if options is not None else default_options()
+    out_dtype = torch.float64 if opts.precision == PREC_FP64 else torch.float32
+    n_lp = offsets.numel() - 1
+    _need(ax, torch.float32, "ax")
+    _need(ay, torch.float32, "ay", ax.numel())
+    _need(b, torch.float32, "b", ax.numel())
+    _need(offsets, torch.int64, "offsets")
+    _need(status_in, torch.int32, "status_in", n_lp)
+    _need(out_xy, out_dtype, "out_xy", 2 * n_lp)
+    _need(out_status, torch.int32, "out_status", n_lp)
+    if out_t is not None:
+        _need(out_t, torch.float32, "out_t", n_lp)
+    wbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(_lib.lp2d_least_violation(_data_ptr(ax), _data_ptr(ay), _data_ptr(b), _ptr(offsets), n_lp, Box(*box),
+                                     _data_ptr(status_in), _data_ptr(out_xy), _ptr(out_t), _data_ptr(out_status),
+                                     ctypes.byref(opts), _ptr(workspace), wbytes, _stream_handle(stream)))

@@ -112,3 +112,18 @@ def farkas_certificate(rows):
     yb = float(y @ R[:, 2])
     assert yb < 0, (y, R)
     return y
+
+
+def least_violation_batch(batch, tmax_factor=8.0):
+    """The least-violation LP of every LP of a 2-D batch as a 3-D batch in (x, y, t):
+    minimise t s.t. a.x - |a| t <= b, (x, y) in the box, 0 <= t <= tmax_factor * max |box|.
+    |a| is the float32 value of sqrt(ax*ax + ay*ay) with each operation rounded."""
+    ax = np.asarray(batch["ax"], np.float32)
+    ay = np.asarray(batch["ay"], np.float32)
+    az = -np.sqrt(ax * ax + ay * ay).astype(np.float32)
+    box = tuple(float(v) for v in batch["box"])
+    tmax = float(np.float32(tmax_factor) * np.float32(max(abs(v) for v in box)))
+    n_lp = len(batch["offsets"]) - 1
+    obj = np.tile(np.array([0.0, 0.0, -1.0], np.float32), (n_lp, 1))
+    return {"ax": ax, "ay": ay, "az": az, "b": np.asarray(batch["b"], np.float32), "offsets": batch["offsets"],
+            "obj": obj, "box": box + (0.0, tmax)}

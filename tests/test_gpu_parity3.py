@@ -142,3 +142,39 @@ def test_results_identical_across_tuning_and_repeated_launches():
         lp2d.solve_batch3d(t["ax"], t["ay"], t["az"], t["b"], t["offsets"], t["obj"], batch["box"], xyz, st, opts, ws)
     torch.cuda.synchronize()
     assert (st.cpu().numpy() == base["status"]).all()
+
+
+def test_least_violation_of_infeasible_2d_lps():
+    import lp_pins
+
+    batch = workloads.ragged(n_lp=20000, hi=1017, seed=31)
+    t = {k: torch.from_numpy(np.ascontiguousarray(batch[k]).reshape(-1)).to(DEV) for k in ("ax", "ay", "b", "offsets", "obj")}
+    n = len(batch["offsets"]) - 1
+    opts = lp2d.default_options(seed=3)
+    ws = lp2d.new_workspace(n, opts, device=DEV)
+    xy = torch.empty(2 * n, device=DEV)
+    st = torch.empty(n, dtype=torch.int32, device=DEV)
+    lp2d.solve_batch_ex(t["ax"], t["ay"], t["b"], t["offsets"], t["obj"], batch["box"], xy, st, opts, ws)
+    st_lv = torch.full((n,), -5, dtype=torch.int32, device=DEV)
+    tt = torch.full((n,), -5.0, device=DEV)
+    lp2d.least_violation(t["ax"], t["ay"], t["b"], t["offsets"], batch["box"], st, xy, st_lv, out_t=tt,
+                         options=lp2d.default_options(seed=3), workspace=ws)
+    torch.cuda.synchronize()
+    st2 = st.cpu().numpy()
+    inf = st2 == oracle.INFEASIBLE
+    assert inf.sum() > 1500
+    lv = lp_pins.least_violation_batch(batch)
+    ref = oracle.solve_batch3(lv["ax"], lv["ay"], lv["az"], lv["b"], lv["offsets"], lv["obj"], lv["box"], seed=3,
+                              threads=THREADS)
+    got_st, got_t, got_xy = st_lv.cpu().numpy(), tt.cpu().numpy(), xy.cpu().numpy().reshape(-1, 2)
+    assert (got_st[~inf] == -5).all() and (got_t[~inf] == -5.0).all()  # untouched
+    assert np.array_equal(got_st[inf], ref["status"][inf])
+    tref = ref["xyz"][inf, 2]
+    assert np.abs(got_t[inf] - tref).max() / max(np.abs(tref).max(), 1.0) <= 1e-4
+    # the returned point violates no constraint by more than its t
+    off = batch["offsets"]
+    for l in np.nonzero(inf)[0][:300]:
+        s, e = off[l], off[l + 1]
+        a = np.stack([batch["ax"][s:e], batch["ay"][s:e]], 1).astype(np.float64)
+        viol = (a @ got_xy[l].astype(np.float64) - batch["b"][s:e]) / np.linalg.norm(a, axis=1)
+        assert viol.max() <= got_t[l] + 1e-3 * max(1.0, abs(got_t[l]))

@@ -171,3 +171,31 @@ def test_violations_grow_like_three_log_m():
         harmonic = sum(1.0 / k for k in range(1, m + 1))
         assert r["nviol"].mean() <= 3.0 * harmonic + 1.0, (m, r["nviol"].mean())
         assert r["nviol"].mean() >= 0.5 * math.log(m), (m, r["nviol"].mean())
+
+
+def test_least_violation_closed_form_and_highs():
+    import lp_pins
+
+    # x <= -1 and x >= 1: the least violation is 1, at x = 0
+    b2 = {"ax": np.array([1, -1], np.float32), "ay": np.array([0, 0], np.float32), "b": np.array([-1, -1], np.float32),
+          "offsets": np.array([0, 2]), "obj": np.array([[1, 0]], np.float32), "box": (-10.0, 10.0, -10.0, 10.0)}
+    lv = lp_pins.least_violation_batch(b2)
+    r = oracle.solve_batch3(lv["ax"], lv["ay"], lv["az"], lv["b"], lv["offsets"], lv["obj"], lv["box"])
+    assert r["status"][0] != oracle.INFEASIBLE
+    assert r["xyz"][0][0] == pytest.approx(0.0, abs=1e-12) and r["xyz"][0][2] == pytest.approx(1.0, rel=1e-12)
+    # infeasible disk-family LPs: the least violation equals HiGHS's minimax value
+    linprog = pytest.importorskip("scipy.optimize").linprog
+    batch = workloads.disk_batch(np.full(80, 30), seed=21, infeasible_frac=0.5)
+    lv = lp_pins.least_violation_batch(batch)
+    r = oracle.solve_batch3(lv["ax"], lv["ay"], lv["az"], lv["b"], lv["offsets"], lv["obj"], lv["box"])
+    checked = 0
+    for l in np.nonzero(batch["infeasible"])[0]:
+        s, e = batch["offsets"][l], batch["offsets"][l + 1]
+        A = np.stack([lv["ax"][s:e], lv["ay"][s:e], lv["az"][s:e]], 1).astype(np.float64)
+        res = linprog([0, 0, 1], A_ub=A, b_ub=lv["b"][s:e].astype(np.float64),
+                      bounds=[(-1e3, 1e3), (-1e3, 1e3), (0, lv["box"][5])], method="highs")
+        assert res.status == 0
+        assert r["xyz"][l][2] == pytest.approx(res.fun, rel=1e-7, abs=1e-7)
+        assert r["xyz"][l][2] > 1e-3  # infeasible: some violation is unavoidable
+        checked += 1
+    assert checked == 40
