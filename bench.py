@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=1.0,
                     help="length of the Poisson request stream of the serving leg (0 skips it)")
+    ap.add_argument("--no-lp3d", action="store_true", help="skip the 3-D solver and least-violation legs")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time only the FP32 solve (no FP64 comparator, e2e or CPU legs); for profiler captures")
     return ap.parse_args()
@@ -173,6 +174,102 @@ def sample_batch(batch, n_lp_sample):
     s, e = int(off[0]), int(off[-1])
     return {"ax": batch["ax"][s:e], "ay": batch["ay"][s:e], "b": batch["b"][s:e], "offsets": off - s,
             "obj": batch["obj"][:n_lp_sample], "box": batch["box"]}
+
+
+def measure_lp3d(args, dev, stream, peak, world):
+    """The batched 3-D solver on the 65,536-LP ragged 3-D batch (CUDA events over
+    repeated launches; inputs 219 MB > L2) and the least-violation fallback on the
+    infeasible LPs of a 2-D ragged batch of at most 1018 constraints per LP."""
+    import torch
+
+    from paper_1902_04995_gb300 import dist as lpdist
+    from paper_1902_04995_gb300 import lp2d, workloads
+
+    b3 = workloads.ragged3d(seed=args.seed)
+    t3 = {k: torch.from_numpy(np.ascontiguousarray(b3[k]).reshape(-1)).to(dev)
+          for k in ("ax", "ay", "az", "b", "offsets", "obj")}
+    n3 = len(b3["offsets"]) - 1
+    opts = lp2d.default_options(seed=args.seed)
+    ws = lp2d.new_workspace(n3, opts, device=dev)
+    xyz = torch.empty(3 * n3, device=dev)
+    st3 = torch.empty(n3, dtype=torch.int32, device=dev)
+
+    def solve3():
+        lp2d.solve_batch3d(t3["ax"], t3["ay"], t3["az"], t3["b"], t3["offsets"], t3["obj"], b3["box"], xyz, st3,
+                           opts, ws, stream=stream)
+
+    def timed(fn, reps):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            stream.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms3 = lpdist.max_over_ranks(timed(solve3, 50), device=dev)
+    algo3 = workloads.algorithmic_bytes(b3)
+    status3 = np.bincount(st3.cpu().numpy(), minlength=4).tolist()
+    # least violation: 2-D ragged batch capped at the 3-D solver's size limit
+    b2 = workloads.ragged(seed=args.seed, hi=1017)
+    t2 = {k: torch.from_numpy(np.ascontiguousarray(b2[k]).reshape(-1)).to(dev) for k in ("ax", "ay", "b", "offsets", "obj")}
+    n2 = len(b2["offsets"]) - 1
+    xy = torch.empty(2 * n2, device=dev)
+    st2 = torch.empty(n2, dtype=torch.int32, device=dev)
+    ws2 = lp2d.new_workspace(n2, opts, device=dev)
+    with torch.cuda.stream(stream):
+        lp2d.solve_batch_ex(t2["ax"], t2["ay"], t2["b"], t2["offsets"], t2["obj"], b2["box"], xy, st2, opts, ws2,
+                            stream=stream)
+    stream.synchronize()
+    st_lv = torch.empty(n2, dtype=torch.int32, device=dev)
+    tviol = torch.empty(n2, device=dev)
+
+    def fallback():
+        lp2d.least_violation(t2["ax"], t2["ay"], t2["b"], t2["offsets"], b2["box"], st2, xy, st_lv, out_t=tviol,
+                             options=opts, workspace=ws2, stream=stream)
+
+    ms_lv = lpdist.max_over_ranks(timed(fallback, 20), device=dev)
+    n_inf = int((st2 == 1).sum().item())
+    line = {
+        "workload": "ragged3d_65536_logu8_1017", "n_lp": n3, "n_constraints": int(b3["offsets"][-1]),
+        "value": n3 * world / (ms3 * 1e-3), "unit": UNIT, "ms_per_step": ms3, "status_counts": status3,
+        "roofline": {"bound": "hbm", "achieved": algo3 / (ms3 * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": algo3 / (ms3 * 1e-3) / 1e9 / peak,
+                     "algorithmic_bytes": algo3, "per_unit": "16 B per constraint + 36 B per LP"},
+        "kernel": "seidel3_kernel<float>", "dtype": "f32",
+        "least_violation": {"workload": "ragged_131072_logu8_1017 (its infeasible LPs)", "infeasible_lps": n_inf,
+                            "ms_per_step": ms_lv, "value": n_inf / (ms_lv * 1e-3), "unit": "infeasible LPs/s",
+                            "kernel": "seidel3_kernel<float> (least-violation mode)"},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+
+        s3 = sample_batch3(b3, 4096)
+        done, t0 = 0, time.perf_counter()
+        while True:
+            oracle.solve_batch3(s3["ax"], s3["ay"], s3["az"], s3["b"], s3["offsets"], s3["obj"], s3["box"],
+                                threads=os.cpu_count() or 1)
+            done += 4096
+            el = time.perf_counter() - t0
+            if el >= 2.0:
+                break
+        line["cpu_baseline"] = {"value": done / el, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+                                "sample": f"first 4096 LPs of the 3-D ragged batch, repeated: {done} LPs in {el:.1f} s"}
+    del t3, t2, xyz, st3, xy, st2
+    torch.cuda.empty_cache()
+    return line
+
+
+def sample_batch3(batch, n_lp_sample):
+    """The first n_lp_sample LPs of a 3-D batch."""
+    off = batch["offsets"][: n_lp_sample + 1]
+    s, e = int(off[0]), int(off[-1])
+    return {"ax": batch["ax"][s:e], "ay": batch["ay"][s:e], "az": batch["az"][s:e], "b": batch["b"][s:e],
+            "offsets": off - s, "obj": batch["obj"][:n_lp_sample], "box": batch["box"]}
 
 
 def run_reference(args):
@@ -361,6 +458,11 @@ def run_ours(args):
             pg.destroy_process_group()
         return
 
+    # ---- the 3-D solver and the least-violation fallback (widened rows of the method)
+    lp3d_line = None
+    if not args.no_lp3d:
+        lp3d_line = measure_lp3d(args, dev, stream, measured_peaks()[0], world)
+
     # ---- serving: Poisson requests (2,000/s) admitted under a 20 GB device cap
     serve_line = None
     if args.serve_seconds > 0:
@@ -430,6 +532,7 @@ def run_ours(args):
                 "serial_ms_per_step": ms_e2e_serial},
         "cpu_baseline": cpu,
         "serve": serve_line,
+        "lp3d": lp3d_line,
         "clocks": clocks,
         "gpu_launches": args.steps,
     }
