@@ -61,11 +61,16 @@ def dist_env():
     return rank, world, local
 
 
-def kernel_source_hash() -> str:
+# the sources the FP32 persistent kernel is compiled from (the entry-point file and the
+# other kernels do not change its code)
+KERNEL_SOURCES = ("lp2d_device.cuh", "lp2d_internal.h", "lp2d_persistent.cu", "lp2d_solve.cuh", "lp2d_staged.cuh")
+
+
+def kernel_source_hash(files=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1902_04995_gb300", "csrc", "*"))):
-        h.update(os.path.basename(f).encode())
-        h.update(open(f, "rb").read())
+    for name in sorted(files):
+        h.update(name.encode())
+        h.update(open(os.path.join(ROOT, "paper_1902_04995_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -341,8 +346,14 @@ def run_ours(args):
     box = batch["box"]
     stream = torch.cuda.Stream(device=dev)
 
-    # ---- FP32 persistent solve, graph-replayed
+    # ---- FP32 persistent solve, autotuned (untimed), graph-replayed
     solver = lp2d.Solver(n_lp, lp2d.default_options(), device=dev)
+    tune = None
+    if not args.kernel_only:
+        tune_ms = solver.autotune(t["ax"], t["ay"], t["b"], t["offsets"], obj, box, reps=2, stream=stream)
+        o = solver.options
+        tune = {"ctas_per_sm": o.ctas_per_sm, "chunk_big": o.chunk_big, "chunk_small": o.chunk_small,
+                "ms_per_solve": tune_ms, "grid": "ctas_per_sm {occ, occ-1} x chunk_big {1,2,4} x chunk_small {1,2,4,8}"}
     with torch.cuda.stream(stream):
         for _ in range(3):
             solver(t["ax"], t["ay"], t["b"], t["offsets"], obj, box)
@@ -375,6 +386,24 @@ def run_ours(args):
     sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
     ms_max = lpdist.max_over_ranks(ms, device=dev)
+    # the same solve captured 100 times in one graph (repeated solves of one batch)
+    graph100_ms = None
+    if not args.kernel_only:
+        g100 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g100, stream=stream):
+            for _ in range(100):
+                solver(t["ax"], t["ay"], t["b"], t["offsets"], obj, box)
+        with torch.cuda.stream(stream):
+            g100.replay()
+            h0 = torch.cuda.Event(enable_timing=True)
+            h1 = torch.cuda.Event(enable_timing=True)
+            h0.record(stream)
+            for _ in range(3):
+                g100.replay()
+            h1.record(stream)
+        stream.synchronize()
+        graph100_ms = h0.elapsed_time(h1) / 300
+        del g100
     # sanity: the timed solves produced a full set of statuses
     st = solver.out_status.cpu().numpy()
     assert ((st >= 0) & (st <= 3)).all()
@@ -533,6 +562,8 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "serve": serve_line,
         "lp3d": lp3d_line,
+        "autotune": tune,
+        "graph100_ms_per_solve": graph100_ms,
         "clocks": clocks,
         "gpu_launches": args.steps,
     }

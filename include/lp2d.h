@@ -229,6 +229,24 @@ int lp2d_solve_batch_host(const float* ax, const float* ay, const float* b, cons
 int lp2d_visit_order(uint64_t seed_l, int64_t m, int64_t* out, lp2d_stream_t stream);
 
 /**
+ * Autotune the persistent schedule for a batch: solve it with each candidate of a
+ * small grid -- ctas_per_sm in {the occupancy limit, one less}, chunk_big in
+ * {1, 2, 4}, chunk_small in {1, 2, 4, 8} -- timing `reps` solves per candidate with
+ * CUDA events on `stream` after one warm-up solve, and write the fastest into
+ * opt->ctas_per_sm / chunk_big / chunk_small (the other fields of *opt are the base
+ * options of every trial; out_nviol / out_def are not written).  The tuned fields
+ * change only the speed: results are the same for every setting.  The arguments
+ * are those of lp2d_solve_batch_ex; out_xy / out_status hold the last trial's
+ * results.  Synchronises `stream`; not for use inside CUDA-graph capture.
+ * out_best_ms (host, may be NULL) receives the winner's time per solve.
+ * Returns an lp2d_err (LP2D_ERR_UNSUPPORTED for the uniform schedule).
+ */
+int lp2d_autotune(const float* ax, const float* ay, const float* b, const int64_t* offsets,
+                  int64_t n_lp, const float* obj_xy, lp2d_box box, void* out_xy, int32_t* out_status,
+                  lp2d_options* opt, void* workspace, size_t workspace_bytes, int reps,
+                  float* out_best_ms, lp2d_stream_t stream);
+
+/**
  * Synchronise `stream`, return the device error word accumulated in `workspace`
  * (LP2D_DEVERR_* bits) through *out_bits, and clear it.  Returns an lp2d_err.
  */

@@ -236,6 +236,74 @@ int lp2d_solve_batch(const float* ax, const float* ay, const float* b, const int
     return lp2d_solve_batch_ex(ax, ay, b, offsets, n_lp, obj_xy, box, out_xy, out_status, nullptr, ws, bytes, stream);
 }
 
+int lp2d_autotune(const float* ax, const float* ay, const float* b, const int64_t* offsets, int64_t n_lp,
+                  const float* obj_xy, lp2d_box box, void* out_xy, int32_t* out_status, lp2d_options* opt,
+                  void* workspace, size_t workspace_bytes, int reps, float* out_best_ms, lp2d_stream_t stream) {
+    if (!opt) return fail(LP2D_ERR_INVALID_ARGUMENT, "opt is NULL (it carries the base options and the result)");
+    if (reps < 1) return fail(LP2D_ERR_INVALID_ARGUMENT, "reps = %d < 1", reps);
+    if (opt->schedule != LP2D_SCHED_PERSISTENT)
+        return fail(LP2D_ERR_UNSUPPORTED, "only the persistent schedule has tuning parameters");
+    lp2d_options base = *opt;
+    base.out_nviol = nullptr;  // the trial solves write only out_xy / out_status
+    base.out_def = nullptr;
+    int rc = lp2d_solve_batch_ex(ax, ay, b, offsets, n_lp, obj_xy, box, out_xy, out_status, &base, workspace,
+                                 workspace_bytes, stream);  // validates everything once
+    if (rc != LP2D_OK) return rc;
+    if (n_lp == 0) return ok();
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return fail(LP2D_ERR_CUDA, "events: %s", cudaGetErrorString(e));
+    DeviceInfo info;
+    rc = device_info(&info);
+    if (rc != LP2D_OK) return rc;
+    const int occ = info.occ[base.precision];
+    const int ctas[2] = {occ, occ > 1 ? occ - 1 : occ};
+    const int bigs[3] = {1, 2, 4};
+    const int smalls[4] = {1, 2, 4, 8};
+    float best = -1.0f;
+    lp2d_options winner = base;
+    for (int ci = 0; ci < 2 && rc == LP2D_OK; ++ci) {
+        if (ci == 1 && ctas[1] == ctas[0]) break;
+        for (int bi = 0; bi < 3 && rc == LP2D_OK; ++bi) {
+            for (int si = 0; si < 4 && rc == LP2D_OK; ++si) {
+                lp2d_options o = base;
+                o.ctas_per_sm = ctas[ci];
+                o.chunk_big = bigs[bi];
+                o.chunk_small = smalls[si];
+                rc = lp2d_solve_batch_ex(ax, ay, b, offsets, n_lp, obj_xy, box, out_xy, out_status, &o, workspace,
+                                         workspace_bytes, stream);  // warm-up
+                if (rc != LP2D_OK) break;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < reps && rc == LP2D_OK; ++r)
+                    rc = lp2d_solve_batch_ex(ax, ay, b, offsets, n_lp, obj_xy, box, out_xy, out_status, &o,
+                                             workspace, workspace_bytes, stream);
+                cudaEventRecord(e1, s);
+                if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+                    rc = fail(LP2D_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+                    break;
+                }
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= static_cast<float>(reps);
+                if (best < 0.0f || ms < best) {
+                    best = ms;
+                    winner = o;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != LP2D_OK) return rc;
+    opt->ctas_per_sm = winner.ctas_per_sm;
+    opt->chunk_big = winner.chunk_big;
+    opt->chunk_small = winner.chunk_small;
+    if (out_best_ms) *out_best_ms = best;
+    return ok();
+}
+
 int lp2d_visit_order(uint64_t seed_l, int64_t m, int64_t* out, lp2d_stream_t stream) {
     if (m < 0 || m > (1ll << 26)) return fail(LP2D_ERR_INVALID_ARGUMENT, "m = %lld out of range [0, 2^26]", (long long)m);
     if (m == 0) return ok();

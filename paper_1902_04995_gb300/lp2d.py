@@ -215,6 +215,12 @@ class Solver:
                        self.workspace, stream)
         return self.out_xy, self.out_status
 
+    def autotune(self, ax, ay, b, offsets, obj, box, reps: int = 3, stream=None) -> float:
+        """Pick this solver's schedule parameters for the given batch (lp2d_autotune);
+        returns the winner's milliseconds per solve."""
+        return autotune(ax, ay, b, offsets, obj, box, self.out_xy, self.out_status, self.options,
+                        self.workspace, reps, stream)
+
 
 _noalloc_ready = False
 
@@ -352,3 +358,27 @@ def least_violation(ax, ay, b, offsets, box, status_in, out_xy, out_status, out_
     _check(_lib.lp2d_least_violation(_data_ptr(ax), _data_ptr(ay), _data_ptr(b), _ptr(offsets), n_lp, Box(*box),
                                      _data_ptr(status_in), _data_ptr(out_xy), _ptr(out_t), _data_ptr(out_status),
                                      ctypes.byref(opts), _ptr(workspace), wbytes, _stream_handle(stream)))
+
+
+_tune_ready = False
+
+
+def autotune(ax, ay, b, offsets, obj, box, out_xy, out_status, options: Options, workspace: torch.Tensor,
+             reps: int = 3, stream=None) -> float:
+    """lp2d_autotune: time a grid of (ctas_per_sm, chunk_big, chunk_small) on this batch
+    and write the fastest into `options` (in place); returns ms per solve of the winner."""
+    global _tune_ready
+    if not _tune_ready:
+        vp, i64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t
+        _lib.lp2d_autotune.argtypes = [vp, vp, vp, vp, i64, vp, Box, vp, vp, ctypes.POINTER(Options), vp, sz,
+                                       ctypes.c_int, ctypes.POINTER(ctypes.c_float), vp]
+        _lib.lp2d_autotune.restype = ctypes.c_int
+        _tune_ready = True
+    out_dtype = torch.float64 if options.precision == PREC_FP64 else torch.float32
+    n_lp = _validate(ax, ay, b, offsets, obj, out_xy, out_status, out_dtype)
+    best = ctypes.c_float(0.0)
+    wbytes = workspace.numel() * workspace.element_size()
+    _check(_lib.lp2d_autotune(_data_ptr(ax), _data_ptr(ay), _data_ptr(b), _ptr(offsets), n_lp, _data_ptr(obj),
+                              Box(*box), _data_ptr(out_xy), _data_ptr(out_status), ctypes.byref(options),
+                              _ptr(workspace), wbytes, int(reps), ctypes.byref(best), _stream_handle(stream)))
+    return float(best.value)

@@ -188,6 +188,24 @@ def test_batches_of_one_size_class(lo, hi, n_lp):
         assert np.array_equal(got["xy"], base["xy"], equal_nan=True), tune
 
 
+def test_autotune_picks_a_grid_point_and_keeps_the_results():
+    batch = workloads.ragged(n_lp=20000)
+    t = to_dev(batch)
+    base = gpu_solve(batch, seed=2)
+    solver = lp2d.Solver(20000, lp2d.default_options(seed=2), device=DEV)
+    ms = solver.autotune(t["ax"], t["ay"], t["b"], t["offsets"], t["obj"].reshape(-1), batch["box"], reps=2)
+    o = solver.options
+    assert ms > 0.0
+    assert o.chunk_big in (1, 2, 4) and o.chunk_small in (1, 2, 4, 8) and o.ctas_per_sm >= 1
+    solver(t["ax"], t["ay"], t["b"], t["offsets"], t["obj"].reshape(-1), batch["box"])
+    torch.cuda.synchronize()
+    assert (solver.out_status.cpu().numpy() == base["status"]).all()
+    assert np.array_equal(solver.out_xy.cpu().numpy().reshape(-1, 2).astype(np.float64), base["xy"], equal_nan=True)
+    with pytest.raises(lp2d.LP2DError):
+        lp2d.autotune(t["ax"], t["ay"], t["b"], t["offsets"], t["obj"].reshape(-1), batch["box"], solver.out_xy,
+                      solver.out_status, lp2d.default_options(schedule=lp2d.SCHED_UNIFORM), solver.workspace)
+
+
 def test_repeated_launches_reuse_workspace_and_graph_replay_is_identical():
     batch = workloads.ragged(n_lp=30000)
     t = to_dev(batch)
