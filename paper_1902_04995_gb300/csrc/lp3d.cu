@@ -394,8 +394,9 @@ __device__ void warp_queue3(const Params3& P, unsigned long long* head, long lon
     }
 }
 
+// FP32: fitted to 6 resident CTAs per SM (the limit of its shared memory).
 template <typename Real>
-__global__ void __launch_bounds__(kWarps3 * 32) seidel3_kernel(const Params3 P) {
+__global__ void __launch_bounds__(kWarps3 * 32, sizeof(Real) == 4 ? 6 : 1) seidel3_kernel(const Params3 P) {
     __shared__ float sX[kStage3];
     __shared__ float sY[kStage3];
     __shared__ float sZ[kStage3];
