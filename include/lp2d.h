@@ -222,9 +222,9 @@ int lp2d_solve_batch_host(const float* ax, const float* ay, const float* b, cons
  * Write the visit order pi of one LP with m constraints and seed seed_l (the seed of
  * LP l is seed + l) into device int64 out[m]: out[k] is the index of the constraint
  * visited at step k.  Runs the same device code the solver uses (Sec. 2.1 asks for a
- * random visit order; the order is a 4-round balanced Feistel network on
- * 2*ceil(ceil(log2 m)/2) bits, at least 2, with SplitMix64 round keys and cycle walking).
- * Returns an lp2d_err.
+ * random visit order; the constraints are visited in increasing order of their keys
+ * under a 4-round balanced Feistel network on 2*ceil(ceil(log2 m)/2) bits, at least 2,
+ * with SplitMix64 round keys).  m <= 2^26; one CTA.  Returns an lp2d_err.
  */
 int lp2d_visit_order(uint64_t seed_l, int64_t m, int64_t* out, lp2d_stream_t stream);
 
