@@ -348,15 +348,18 @@ __device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cy
         const Real fs = (cu > Real(0)) ? Real(1) : Real(-1);
         const Real ux = -ly * fs, uy = lx * fs;
         MixedLine ml{0.0, 0.0, 0.0f};
-        if constexpr (kMixed) {
+        // the foot of l in FP64, computed only when a near-parallel pair or a grazing
+        // interval needs it (FP64 division is slow on this GPU)
+        auto foot64 = [&]() {
             const double lx64 = lx, ly64 = ly, sc64 = static_cast<double>(lb) / (lx64 * lx64 + ly64 * ly64);
             ml.p0x = lx64 * sc64;
             ml.p0y = ly64 * sc64;
-            ml.lim = P.tau * P.tau * static_cast<float>(nrm2);
-        }
+        };
+        if constexpr (kMixed) ml.lim = P.tau * P.tau * static_cast<float>(nrm2);
         Real thi = real_inf<Real>(), tlo = -real_inf<Real>();
         int phi = kNoPos;
         if (kTeam && fslot >= kTeamMinSlots) {
+            if constexpr (kMixed) foot64();
             if (lane == 0) {
                 job->cmd = kJobRun;
                 job->fslot = fslot;
@@ -391,6 +394,7 @@ __device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cy
             wu_range<Real, 32, kMixed>(sX, sY, sB, lane, fslot, p0x, p0y, ux, uy, thi, phi, tlo, ml, &np);
             if (kMixed && __any_sync(kFull, np)) {
                 // a near-parallel pair: redo this 1-D LP with FP64 intersections for them
+                foot64();
                 thi = real_inf<Real>();
                 tlo = -real_inf<Real>();
                 phi = kNoPos;
@@ -405,6 +409,7 @@ __device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cy
             // a grazing interval (ends within FP32 rounding of each other): decide the
             // 1-D LP again in FP64 before trusting emptiness or the endpoint
             if (!empty && (thi - tlo) <= Real(1e-5) * (real_abs(thi) + real_abs(tlo) + Real(1))) {
+                foot64();
                 double th64 = real_inf<double>(), tl64 = -real_inf<double>();
                 int ph64 = kNoPos;
                 wu_range<double, 32>(sX, sY, sB, lane, fslot, ml.p0x, ml.p0y, static_cast<double>(ux),
