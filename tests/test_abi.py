@@ -151,6 +151,28 @@ def test_3d_host_side_validation(lib):
     assert "workspace" in lib.last_error()
 
 
+def test_autotune_host_side_validation(lib):
+    L = lib._lib
+    vp, i64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t
+    L.lp2d_autotune.argtypes = [vp, vp, vp, vp, i64, vp, lib.Box, vp, vp, ctypes.POINTER(lib.Options), vp, sz,
+                                ctypes.c_int, ctypes.POINTER(ctypes.c_float), vp]
+    L.lp2d_autotune.restype = ctypes.c_int
+    box = lib.Box(-1, 1, -1, 1)
+    o = lib.default_options()
+    assert L.lp2d_autotune(None, None, None, None, 0, None, box, None, None, None, None, 0, 2, None,
+                           None) == lib.ERR_INVALID_ARGUMENT  # no options
+    assert L.lp2d_autotune(None, None, None, None, 0, None, box, None, None, ctypes.byref(o), None, 0, 0, None,
+                           None) == lib.ERR_INVALID_ARGUMENT  # reps < 1
+    u = lib.default_options(schedule=lib.SCHED_UNIFORM)
+    assert L.lp2d_autotune(None, None, None, None, 0, None, box, None, None, ctypes.byref(u), None, 0, 2, None,
+                           None) == lib.ERR_UNSUPPORTED
+    assert L.lp2d_autotune(None, None, None, None, -1, None, box, None, None, ctypes.byref(o), None, 0, 2, None,
+                           None) == lib.ERR_INVALID_ARGUMENT
+    assert L.lp2d_autotune(None, None, None, None, 0, None, box, None, None, ctypes.byref(o), None, 0, 2, None,
+                           None) == lib.OK  # an empty batch has nothing to tune
+    assert (o.ctas_per_sm, o.chunk_big, o.chunk_small) == (0, 0, 0)
+
+
 def test_product_path_does_not_import_the_oracle():
     pkg = os.path.join(ROOT, "paper_1902_04995_gb300")
     for dirpath, _, files in os.walk(pkg):

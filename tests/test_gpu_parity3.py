@@ -178,3 +178,37 @@ def test_least_violation_of_infeasible_2d_lps():
         a = np.stack([batch["ax"][s:e], batch["ay"][s:e]], 1).astype(np.float64)
         viol = (a @ got_xy[l].astype(np.float64) - batch["b"][s:e]) / np.linalg.norm(a, axis=1)
         assert viol.max() <= got_t[l] + 1e-3 * max(1.0, abs(got_t[l]))
+
+
+def test_least_violation_in_fp64():
+    import lp_pins
+
+    batch = workloads.disk_batch(np.full(3000, 80), seed=41, infeasible_frac=0.3)
+    t = {k: torch.from_numpy(np.ascontiguousarray(batch[k]).reshape(-1)).to(DEV) for k in ("ax", "ay", "b", "offsets", "obj")}
+    n = len(batch["offsets"]) - 1
+    st = torch.from_numpy(np.where(batch["infeasible"], 1, 0).astype(np.int32)).to(DEV)
+    xy = torch.full((2 * n,), 7.0, dtype=torch.float64, device=DEV)
+    st_lv = torch.full((n,), -5, dtype=torch.int32, device=DEV)
+    tt = torch.full((n,), -5.0, device=DEV)
+    opts = lp2d.default_options(precision=lp2d.PREC_FP64, seed=4)
+    lp2d.least_violation(t["ax"], t["ay"], t["b"], t["offsets"], batch["box"], st, xy, st_lv, out_t=tt,
+                         options=opts, workspace=lp2d.new_workspace(n, opts, device=DEV))
+    torch.cuda.synchronize()
+    inf = batch["infeasible"]
+    lv = lp_pins.least_violation_batch(batch)
+    ref = oracle.solve_batch3(lv["ax"], lv["ay"], lv["az"], lv["b"], lv["offsets"], lv["obj"], lv["box"], seed=4,
+                              threads=THREADS)
+    got_st, got_xy = st_lv.cpu().numpy(), xy.cpu().numpy().reshape(-1, 2)
+    assert np.array_equal(got_st[inf], ref["status"][inf])
+    assert (got_st[~inf] == -5).all() and (got_xy[~inf] == 7.0).all()
+    f_ref = ref["xyz"][inf, 2]
+    # the FP64 run reproduces the oracle's least violation (t is returned in float32)
+    assert np.abs(tt.cpu().numpy()[inf] - f_ref).max() <= 1e-6 * max(1.0, np.abs(f_ref).max())
+    # the returned point violates no constraint by more than the least violation
+    off = batch["offsets"]
+    for l in np.nonzero(inf)[0][:200]:
+        s0, e0 = off[l], off[l + 1]
+        a = np.stack([batch["ax"][s0:e0], batch["ay"][s0:e0]], 1).astype(np.float64)
+        # |a| as the least-violation LP defines it (float32)
+        viol = (a @ got_xy[l] - batch["b"][s0:e0]) / -lv["az"][s0:e0].astype(np.float64)
+        assert viol.max() <= ref["xyz"][l, 2] + 1e-9
