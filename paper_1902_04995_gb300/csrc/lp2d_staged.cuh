@@ -389,6 +389,37 @@ __device__ void drive_lp(const Params& P, int64_t lp, int m, float cxf, float cy
             }
             thi = KT::val(khi);
             tlo = KT::val(klo);
+        } else if (!kMixed && fslot <= 32) {
+            // a short 1-D LP: one slot per lane, no loop
+            if (lane < fslot) {
+                const Real gx = sX[lane], gy = sY[lane], gb = sB[lane];
+                const Real den = (gx * ux + gy * uy) + Real(0);
+                const Real num = gb - (gx * p0x + gy * p0y);
+                const Real t = real_div<Real>(num, den);
+                const bool right = den >= Real(0);
+                if (right && t < thi) { thi = t; phi = lane; }
+                tlo = right ? tlo : t;
+            }
+            warp_reduce_1dlp<Real>(thi, phi, tlo);
+        } else if (!kMixed && fslot <= 64) {
+            // a short 1-D LP: at most two slots per lane, no loop
+            const Real ninf = -real_inf<Real>();
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = lane + 32 * h;
+                if (j < fslot) {
+                    const Real gx = sX[j], gy = sY[j], gb = sB[j];
+                    const Real den = (gx * ux + gy * uy) + Real(0);
+                    const Real num = gb - (gx * p0x + gy * p0y);
+                    const Real t = real_div<Real>(num, den);
+                    const bool right = den >= Real(0);
+                    const bool take = right && (t < thi);
+                    thi = take ? t : thi;
+                    phi = take ? j : phi;
+                    tlo = real_max<Real>(tlo, right ? ninf : t);
+                }
+            }
+            warp_reduce_1dlp<Real>(thi, phi, tlo);
         } else {
             bool np = false;
             wu_range<Real, 32, kMixed>(sX, sY, sB, lane, fslot, p0x, p0y, ux, uy, thi, phi, tlo, ml, &np);
