@@ -5,9 +5,10 @@ import this package.  The product path (``paper_1902_04995_gb300``) never import
 it, and it imports nothing from the product.
 
 The arithmetic lives in ``seidel_oracle.c`` (plain serial Seidel in FP64, Sec. 2.1 of
-the paper, Eqs. 1-4) and ``seidel3_oracle.c`` (the same method in three dimensions,
-the direction Sec. 6 names); this module only builds them with gcc and marshals numpy
-arrays through ctypes.  ctypes drops the GIL during a call, so ``threads > 1`` splits a
+the paper, Eqs. 1-4), ``seidel3_oracle.c`` (the same method in three dimensions, the
+direction Sec. 6 names) and ``seidelN_oracle.c`` (any dimension up to five, as a
+recursion over affine subspaces); this module only builds them with gcc and marshals
+numpy arrays through ctypes.  ctypes drops the GIL during a call, so ``threads > 1`` splits a
 batch by LP range over plain Python threads (one serial solve per LP, no change to
 the arithmetic).
 """
@@ -21,7 +22,7 @@ from concurrent.futures import ThreadPoolExecutor
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "seidel_oracle.c"), os.path.join(_HERE, "seidel3_oracle.c")]
+_SRCS = [os.path.join(_HERE, f) for f in ("seidel_oracle.c", "seidel3_oracle.c", "seidelN_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
 OPTIMAL, INFEASIBLE, BOX_BOUNDED, BAD_INPUT = 0, 1, 2, 3
@@ -65,6 +66,8 @@ def _load():
                                        vp, vp, vp, vp]
     lib.oracle_solve_batch3.restype = None
     lib.oracle_solve_batch3.argtypes = [vp, vp, vp, vp, vp, i64, i64, vp, vp, u64, dbl, vp, vp, vp, vp]
+    lib.oracle_solve_batchN.restype = None
+    lib.oracle_solve_batchN.argtypes = [ctypes.c_int, vp, vp, vp, i64, i64, vp, vp, u64, dbl, vp, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -192,6 +195,50 @@ def solve_batch3(ax, ay, az, b, offsets, obj, box, seed: int = 0, eps: float = E
         with ThreadPoolExecutor(max_workers=threads) as ex:
             list(ex.map(lambda ab: run(*ab), _split(offsets, 0, n_lp, threads)))
     out = {"xyz": xyz, "status": status}
+    if want_def:
+        out["def"] = dfn
+    if want_nviol:
+        out["nviol"] = nviol
+    return out
+
+
+def solve_batchN(a, b, offsets, obj, box, seed: int = 0, eps: float = EPS_FP64,
+                 threads: int = 1, want_def: bool = False, want_nviol: bool = False):
+    """Solve every d-dimensional LP of a CSR batch serially in FP64 (seidelN_oracle.c).
+
+    a: float32 [d, n_constraints] (row t holds coefficient t of every constraint);
+    b: float32 [n_constraints]; offsets: int64 [n_lp + 1]; obj: float32 [n_lp, d];
+    box: (min_0, max_0, ..., min_{d-1}, max_{d-1}).  Returns a dict with ``x`` (float64
+    [n_lp, d]), ``status`` and optionally ``def`` (int32 [n_lp, d]) and ``nviol``
+    (violations in the whole space, each one an LP of dimension d - 1).
+    """
+    lib = _load()
+    a = np.asarray(a, dtype=np.float32)
+    d = a.shape[0]
+    assert 1 <= d <= 5
+    rows = np.ascontiguousarray(a.T)  # [n_constraints][d]
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    obj = np.ascontiguousarray(obj, dtype=np.float32).reshape(-1)
+    n_lp = offsets.shape[0] - 1
+    assert obj.shape[0] == d * n_lp
+    boxd = np.asarray([float(np.float32(v)) for v in box], dtype=np.float64)
+    assert boxd.shape[0] == 2 * d
+    x = np.zeros((n_lp, d), dtype=np.float64)
+    status = np.zeros(n_lp, dtype=np.int32)
+    dfn = np.zeros((n_lp, d), dtype=np.int32) if want_def else None
+    nviol = np.zeros(n_lp, dtype=np.int64) if want_nviol else None
+
+    def run(lo, hi):
+        lib.oracle_solve_batchN(d, _ptr(rows), _ptr(b), _ptr(offsets), lo, hi, _ptr(obj), _ptr(boxd),
+                                seed & (2**64 - 1), eps, _ptr(x), _ptr(status), _ptr(dfn), _ptr(nviol))
+
+    if threads <= 1 or n_lp < 2 * threads:
+        run(0, n_lp)
+    else:
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(lambda ab: run(*ab), _split(offsets, 0, n_lp, threads)))
+    out = {"x": x, "status": status}
     if want_def:
         out["def"] = dfn
     if want_nviol:

@@ -36,6 +36,14 @@ Sphere family (the 3-D workloads; constraint i is ax[i] x + ay[i] y + az[i] z <=
   around c is feasible; the objective is a unit vector uniform on the sphere.  An LP
   is made infeasible with  -u.x <= -(H + 1),  H = sum of lambda_k b_k over three stored
   normals with u = sum lambda_k n_k, lambda >= 0 (weak duality bounds u.x by H).
+
+Ball family (d = 2..5 dimensions; ``a`` is float32 [d, n_constraints], row t holding
+coefficient t of every constraint, ``obj`` is [n_lp, d] and ``box`` has 2d entries):
+  the sphere family in d dimensions: centre c ~ U[-1,1]^d, unit normals uniform on the
+  sphere, r ~ U[0.5, 2], b = r + n.c, unit objective uniform on the sphere.  An LP is
+  made infeasible with  -u.x <= -(H + 1)  for u = sum_k lambda_k n_k / |.| over d
+  distinct stored normals drawn at random, lambda_k ~ U[0.1, 1] and
+  H = sum_k lambda_k b_k / |sum_k lambda_k n_k| (weak duality bounds u.x by H).
 """
 from __future__ import annotations
 
@@ -321,6 +329,70 @@ def ragged3d(seed=DEFAULT_SEED, n_lp=65536, lo=8, hi=1017):
     return sphere_batch(sizes, seed=seed, infeasible_frac=0.1)
 
 
+def ball_batch(d, sizes, seed=DEFAULT_SEED, infeasible_frac=0.0, box=None):
+    """A batch of d-dimensional ball-family LPs with the given constraint counts.
+
+    A fraction ``infeasible_frac`` of the LPs (a seeded sample among those with at
+    least max(8, d) constraints) gets one appended exclusion constraint."""
+    sizes = np.asarray(sizes, dtype=np.int64)
+    box = tuple(float(v) for v in (box if box is not None else (-BOX_M, BOX_M) * d))
+    assert 1 <= d <= 5 and len(box) == 2 * d
+    rng = np.random.default_rng(seed)
+    n_lp = sizes.shape[0]
+    offsets = np.zeros(n_lp + 1, dtype=np.int64)
+    np.cumsum(sizes, out=offsets[1:])
+    total = int(offsets[-1])
+    centre = rng.uniform(-1.0, 1.0, size=(n_lp, d))
+    nrm = rng.normal(size=(total, d))
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    r = rng.uniform(0.5, 2.0, size=total)
+    owner = np.repeat(np.arange(n_lp), sizes)
+    bb = r + np.einsum("ij,ij->i", nrm, centre[owner])
+    obj = rng.normal(size=(n_lp, d))
+    obj /= np.linalg.norm(obj, axis=1, keepdims=True)
+    n32 = nrm.astype(np.float32)
+    b32 = bb.astype(np.float32)
+    eligible = np.nonzero(sizes >= max(8, d))[0]
+    n_inf = min(int(round(infeasible_frac * n_lp)), eligible.shape[0])
+    infeasible = np.zeros(n_lp, dtype=bool)
+    extra = {}
+    if n_inf > 0:
+        pick = np.sort(eligible[rng.choice(eligible.shape[0], size=n_inf, replace=False)])
+        infeasible[pick] = True
+        for l in pick:
+            s = offsets[l]
+            idx = s + rng.choice(int(sizes[l]), size=d, replace=False)
+            lam = rng.uniform(0.1, 1.0, size=d)
+            u = lam @ n32[idx].astype(np.float64)
+            h = float(lam @ b32[idx].astype(np.float64))
+            nu = float(np.linalg.norm(u))
+            extra[int(l)] = ((-u / nu).astype(np.float32), np.float32(-(h / nu + 1.0)))
+    new_sizes = sizes + infeasible.astype(np.int64)
+    new_off = np.zeros(n_lp + 1, dtype=np.int64)
+    np.cumsum(new_sizes, out=new_off[1:])
+    dst = np.arange(total, dtype=np.int64) + np.repeat(new_off[:-1] - offsets[:-1], sizes)
+    a = np.empty((d, int(new_off[-1])), np.float32)
+    bo = np.empty(int(new_off[-1]), np.float32)
+    a[:, dst] = n32.T
+    bo[dst] = b32
+    for l, (pa, pb) in extra.items():
+        slot = new_off[l + 1] - 1
+        a[:, slot] = pa
+        bo[slot] = pb
+    return {"a": a, "b": bo, "offsets": new_off, "obj": obj.astype(np.float32), "box": box,
+            "infeasible": infeasible}
+
+
+def ragged_nd(d, seed=DEFAULT_SEED, n_lp=65536, lo=8, hi=None):
+    """65,536 ball-family LPs in d dimensions with sizes log-uniform in [8, hi]
+    (default 1023 - 2d, so that with the appended constraint of the 10 % made
+    infeasible no LP exceeds the d-dimensional solver's 1024 - 2d)."""
+    hi = 1023 - 2 * d if hi is None else hi
+    size_rng = np.random.default_rng(seed ^ (0xD0D0 + d))
+    sizes = loguniform_sizes(size_rng, n_lp, lo, hi)
+    return ball_batch(d, sizes, seed=seed, infeasible_frac=0.1)
+
+
 WORKLOADS = {
     "plain_small_256x64": plain_small,
     "plain_65536x256": plain_at_scale,
@@ -332,9 +404,13 @@ WORKLOADS = {
 def algorithmic_bytes(batch) -> int:
     """Bytes one solve must move at minimum: 12 B per constraint read once, plus per
     LP 8 B objective, 8 B offset, 8 B result point and 4 B status (3-D: 16 B per
-    constraint and 12 + 8 + 12 + 4 B per LP)."""
+    constraint and 12 + 8 + 12 + 4 B per LP; d dimensions: 4d + 4 B per constraint and
+    4d + 8 + 4d + 4 B per LP)."""
     n_c = int(batch["offsets"][-1] - batch["offsets"][0])
     n_lp = int(batch["offsets"].shape[0] - 1)
+    if "a" in batch:
+        d = int(batch["a"].shape[0])
+        return (4 * d + 4) * n_c + (8 * d + 12) * n_lp
     if "az" in batch:
         return 16 * n_c + 36 * n_lp
     return 12 * n_c + 28 * n_lp
