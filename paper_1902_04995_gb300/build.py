@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblp2d.so")
-SOURCES = ["lp2d_api.cu", "lp2d_persistent.cu", "lp2d_uniform.cu", "lp2d_noalloc.cu", "lp3d.cu"]
+SOURCES = ["lp2d_api.cu", "lp2d_persistent.cu", "lp2d_uniform.cu", "lp2d_noalloc.cu", "lp3d.cu", "lpnd.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -32,6 +32,7 @@ def _inputs():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     files.append(os.path.join(ROOT, "include", "lp2d.h"))
     files.append(os.path.join(ROOT, "include", "lp3d.h"))
+    files.append(os.path.join(ROOT, "include", "lpnd.h"))
     files.append(os.path.abspath(__file__))
     return files
 

@@ -326,6 +326,59 @@ def solve_batch3d(ax, ay, az, b, offsets, obj, box, out_xyz, out_status, options
                                     ctypes.byref(opts), _ptr(workspace), wbytes, _stream_handle(stream)))
 
 
+_nd_ready = False
+MAX_DIM = 5
+
+
+def max_constraints_nd(d: int) -> int:
+    """LPND_MAX_CONSTRAINTS(d): the largest LP the d-dimensional solver stages."""
+    return 1024 - 2 * d
+
+
+def solve_batch_nd(a, b, offsets, obj, box, out_x, out_status, options: Options | None = None,
+                   workspace: torch.Tensor | None = None, stream=None):
+    """lpnd_solve_batch: the batched d-dimensional solver (2 <= d <= 5).
+
+    a: float32 CUDA tensor [d, n_constraints] (row t: coefficient t of every
+    constraint) or a sequence of d such 1-D tensors; b float32 [n_constraints];
+    offsets int64 [n_lp + 1]; obj float32 [d*n_lp]; box: 2d floats (min_0, max_0,
+    min_1, ...); out_x float32 [d*n_lp] (float64 for PREC_FP64); out_status int32
+    [n_lp]; workspace as for solve_batch_ex (see new_workspace)."""
+    global _nd_ready
+    if not _nd_ready:
+        vp, i64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t
+        _lib.lpnd_solve_batch.argtypes = [ctypes.c_int, vp, vp, vp, i64, vp, vp, vp, vp, ctypes.POINTER(Options),
+                                          vp, sz, vp]
+        _lib.lpnd_solve_batch.restype = ctypes.c_int
+        _nd_ready = True
+    cols = [a[t] for t in range(a.shape[0])] if isinstance(a, torch.Tensor) else list(a)
+    d = len(cols)
+    if not 2 <= d <= MAX_DIM:
+        raise ValueError(f"d = {d} is outside 2..{MAX_DIM}")
+    opts = options if options is not None else default_options()
+    out_dtype = torch.float64 if opts.precision == PREC_FP64 else torch.float32
+    n_lp = offsets.numel() - 1
+    if n_lp < 0:
+        raise ValueError("offsets needs n_lp + 1 entries")
+    _need(cols[0], torch.float32, "a[0]")
+    for t in range(1, d):
+        _need(cols[t], torch.float32, f"a[{t}]", cols[0].numel())
+    _need(b, torch.float32, "b", cols[0].numel())
+    _need(offsets, torch.int64, "offsets")
+    _need(obj, torch.float32, "obj", d * n_lp)
+    _need(out_x, out_dtype, "out_x", d * n_lp)
+    _need(out_status, torch.int32, "out_status", n_lp)
+    if len(box) != 2 * d:
+        raise ValueError(f"box needs {2 * d} values")
+    ptrs = (ctypes.c_void_p * d)(*[_data_ptr(c).value for c in cols])
+    box_c = (ctypes.c_float * (2 * d))(*[float(v) for v in box])
+    wbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(_lib.lpnd_solve_batch(d, ctypes.cast(ptrs, ctypes.c_void_p), _data_ptr(b), _ptr(offsets), n_lp,
+                                 _data_ptr(obj), ctypes.cast(box_c, ctypes.c_void_p), _data_ptr(out_x),
+                                 _data_ptr(out_status), ctypes.byref(opts), _ptr(workspace), wbytes,
+                                 _stream_handle(stream)))
+
+
 _lv_ready = False
 LEAST_VIOLATION_TMAX_FACTOR = 8.0
 

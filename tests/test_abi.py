@@ -9,7 +9,7 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADERS = [os.path.join(ROOT, "include", h) for h in ("lp2d.h", "lp3d.h")]
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("lp2d.h", "lp3d.h", "lpnd.h")]
 
 
 @pytest.fixture(scope="module")
@@ -26,13 +26,13 @@ def lib():
 def declared_functions():
     text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(lp[23]d_[a-z_0-9]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(lp[23n]d_[a-z_0-9]+)\s*\(", text)))
 
 
 def test_header_declares_the_entry_points():
     names = declared_functions()
     for n in ("lp2d_solve_batch", "lp2d_solve_batch_ex", "lp2d_workspace_bytes", "lp2d_visit_order",
-              "lp2d_last_error", "lp2d_read_device_error", "lp3d_solve_batch_ex"):
+              "lp2d_last_error", "lp2d_read_device_error", "lp3d_solve_batch_ex", "lpnd_solve_batch"):
         assert n in names
 
 
@@ -149,6 +149,36 @@ def test_3d_host_side_validation(lib):
     al = ctypes.c_void_p(0x1000)
     assert call(3, p=al) == lib.ERR_WORKSPACE
     assert "workspace" in lib.last_error()
+
+
+def test_nd_host_side_validation(lib):
+    L = lib._lib
+    vp, i64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t
+    L.lpnd_solve_batch.argtypes = [ctypes.c_int, vp, vp, vp, i64, vp, vp, vp, vp, ctypes.POINTER(lib.Options), vp,
+                                   sz, vp]
+    L.lpnd_solve_batch.restype = ctypes.c_int
+
+    def call(d, n, box=None, o=None, a=None, p=None, ws=None, wsb=0, no_box=False):
+        vals = box if box is not None else [-1.0, 1.0] * d
+        bx = None if no_box else (ctypes.c_float * len(vals))(*vals)
+        return L.lpnd_solve_batch(d, a, p, p, n, p, bx, p, p, ctypes.byref(o) if o else None, ws, wsb, None)
+
+    assert call(1, 3) == lib.ERR_INVALID_ARGUMENT and "d = 1" in lib.last_error()
+    assert call(6, 3) == lib.ERR_INVALID_ARGUMENT
+    assert call(4, -1) == lib.ERR_INVALID_ARGUMENT
+    assert call(4, 3, no_box=True) == lib.ERR_INVALID_ARGUMENT
+    assert call(4, 3, box=[-1, 1, -1, 1, 1, -1, -1, 1]) == lib.ERR_INVALID_ARGUMENT and "axis 2" in lib.last_error()
+    assert call(5, 3, box=[-1, 1] * 4 + [-1, float("inf")]) == lib.ERR_INVALID_ARGUMENT
+    assert call(4, 3, o=lib.default_options(precision=lib.PREC_FP32_F64ISECT)) == lib.ERR_UNSUPPORTED
+    assert call(4, 3, o=lib.default_options(schedule=lib.SCHED_UNIFORM)) == lib.ERR_UNSUPPORTED
+    assert call(4, 0) == lib.OK
+    assert call(4, 3) == lib.ERR_INVALID_ARGUMENT  # NULL data
+    al = 0x1000  # aligned fake device addresses: the host reads the pointer values only
+    assert call(4, 3, a=(ctypes.c_void_p * 4)(al, al, al, al), p=ctypes.c_void_p(al)) == lib.ERR_WORKSPACE
+    assert call(4, 3, a=(ctypes.c_void_p * 4)(al, al, None, al), p=ctypes.c_void_p(al)) == lib.ERR_INVALID_ARGUMENT
+    assert "a[2]" in lib.last_error()
+    assert call(4, 3, a=(ctypes.c_void_p * 4)(al, al, al, al + 2), p=ctypes.c_void_p(al)) == lib.ERR_INVALID_ARGUMENT
+    assert lib.max_constraints_nd(5) == 1014
 
 
 def test_autotune_host_side_validation(lib):
