@@ -5,7 +5,9 @@ One step = one solve of the whole ragged batch (131,072 LPs, sizes log-uniform i
 replayed from a CUDA graph with the inputs resident in HBM (579 MB > the 129 MB L2,
 so no flush is needed between steps).  Reported beside it, on the same inputs: the
 plain uniform-launch FP64 solver, the end-to-end rate through the C ABI with
-host-resident buffers, and the FP64 CPU oracle on the host cores.
+host-resident buffers, the FP64 CPU oracle on the host cores, and the widened rows:
+serving, the 3-D solver with the least-violation fallback, and the 4-D and 5-D
+solvers.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -49,6 +51,12 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=1.0,
                     help="length of the Poisson request stream of the serving leg (0 skips it)")
     ap.add_argument("--no-lp3d", action="store_true", help="skip the 3-D solver and least-violation legs")
+    ap.add_argument("--no-lpnd", action="store_true", help="skip the 4-D and 5-D solver legs")
+    ap.add_argument("--lpnd-only", type=int, default=0, metavar="D",
+                    help="only solve a d-dimensional ragged batch three times (for profiler captures)")
+    ap.add_argument("--lpnd-lps", type=int, default=65536, help="LPs of the --lpnd-only batch")
+    ap.add_argument("--lp3d-only", action="store_true",
+                    help="only solve the 65,536-LP ragged 3-D batch three times (for profiler captures)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time only the FP32 solve (no FP64 comparator, e2e or CPU legs); for profiler captures")
     return ap.parse_args()
@@ -64,6 +72,8 @@ def dist_env():
 # the sources the FP32 persistent kernel is compiled from (the entry-point file and the
 # other kernels do not change its code)
 KERNEL_SOURCES = ("lp2d_device.cuh", "lp2d_internal.h", "lp2d_persistent.cu", "lp2d_solve.cuh", "lp2d_staged.cuh")
+KERNEL_SOURCES_3D = ("lp2d_device.cuh", "lp2d_internal.h", "lp2d_staged.cuh", "lp3d.cu")
+KERNEL_SOURCES_ND = ("lp2d_device.cuh", "lp2d_internal.h", "lp2d_staged.cuh", "lpnd.cu")
 
 
 def kernel_source_hash(files=KERNEL_SOURCES) -> str:
@@ -74,10 +84,10 @@ def kernel_source_hash(files=KERNEL_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
+def profiled_traffic(workload: str, files=KERNEL_SOURCES):
     """DRAM bytes per launch recorded by an ncu capture of the current kernel source,
     from the summaries under profiles/ (None when no capture matches the source)."""
-    src = kernel_source_hash()
+    src = kernel_source_hash(files)
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         text = open(path).read()
         m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", text)
@@ -244,7 +254,8 @@ def measure_lp3d(args, dev, stream, peak, world):
         "value": n3 * world / (ms3 * 1e-3), "unit": UNIT, "ms_per_step": ms3, "status_counts": status3,
         "roofline": {"bound": "hbm", "achieved": algo3 / (ms3 * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": algo3 / (ms3 * 1e-3) / 1e9 / peak,
-                     "algorithmic_bytes": algo3, "per_unit": "16 B per constraint + 36 B per LP"},
+                     "algorithmic_bytes": algo3, "per_unit": "16 B per constraint + 36 B per LP",
+                     "traffic": profiled_traffic("ragged3d_65536_logu8_1017", KERNEL_SOURCES_3D)},
         "kernel": "seidel3_kernel<float>", "dtype": "f32",
         "least_violation": {"workload": "ragged_131072_logu8_1017 (its infeasible LPs)", "infeasible_lps": n_inf,
                             "ms_per_step": ms_lv, "value": n_inf / (ms_lv * 1e-3), "unit": "infeasible LPs/s",
@@ -267,6 +278,131 @@ def measure_lp3d(args, dev, stream, peak, world):
     del t3, t2, xyz, st3, xy, st2
     torch.cuda.empty_cache()
     return line
+
+
+def measure_lpnd(args, dev, stream, peak, world, dims=(4, 5)):
+    """The batched d-dimensional solver on the 65,536-LP ragged ball batches of
+    dimension 4 and 5 (CUDA events over repeated launches; inputs 273 / 329 MB > L2),
+    each with the d-dimensional FP64 oracle on a bounded sample of its LPs."""
+    import torch
+
+    from paper_1902_04995_gb300 import dist as lpdist
+    from paper_1902_04995_gb300 import lp2d, workloads
+
+    lines = {}
+    for d in dims:
+        bd = workloads.ragged_nd(d, seed=args.seed)
+        a = torch.from_numpy(bd["a"]).to(dev)
+        b = torch.from_numpy(bd["b"]).to(dev)
+        off = torch.from_numpy(bd["offsets"]).to(dev)
+        obj = torch.from_numpy(bd["obj"].reshape(-1)).to(dev)
+        n = len(bd["offsets"]) - 1
+        opts = lp2d.default_options(seed=args.seed)
+        ws = lp2d.new_workspace(n, opts, device=dev)
+        x = torch.empty(d * n, device=dev)
+        st = torch.empty(n, dtype=torch.int32, device=dev)
+        reps = 20 if d <= 4 else 5
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                lp2d.solve_batch_nd(a, b, off, obj, bd["box"], x, st, opts, ws, stream=stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                lp2d.solve_batch_nd(a, b, off, obj, bd["box"], x, st, opts, ws, stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+        ms = lpdist.max_over_ranks(e0.elapsed_time(e1) / reps, device=dev)
+        algo = workloads.algorithmic_bytes(bd)
+        line = {
+            "workload": f"ragged{d}d_65536_logu8_{1023 - 2 * d}", "n_lp": n, "n_constraints": int(bd["offsets"][-1]),
+            "value": n * world / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "status_counts": np.bincount(st.cpu().numpy(), minlength=4).tolist(),
+            "roofline": {"bound": "hbm", "achieved": algo / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": algo / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes": algo,
+                         "per_unit": f"{4 * d + 4} B per constraint + {8 * d + 12} B per LP",
+                         "traffic": profiled_traffic(f"ragged{d}d_65536_logu8_{1023 - 2 * d}", KERNEL_SOURCES_ND)},
+            "kernel": f"seidel_nd_kernel<float, {d}>", "dtype": "f32",
+        }
+        if not args.no_cpu_baseline and world == 1:
+            import oracle
+
+            oracle.build()
+            n_s = 1024 if d <= 4 else 256
+            s_end = int(bd["offsets"][n_s])
+            sub = {"a": bd["a"][:, :s_end], "b": bd["b"][:s_end], "offsets": bd["offsets"][:n_s + 1],
+                   "obj": bd["obj"][:n_s], "box": bd["box"]}
+            done, t0 = 0, time.perf_counter()
+            while True:
+                oracle.solve_batchN(sub["a"], sub["b"], sub["offsets"], sub["obj"], sub["box"],
+                                    threads=os.cpu_count() or 1)
+                done += n_s
+                el = time.perf_counter() - t0
+                if el >= 2.0:
+                    break
+            line["cpu_baseline"] = {"value": done / el, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+                                    "sample": f"first {n_s} LPs of the {d}-D ragged batch, repeated: {done} LPs "
+                                              f"in {el:.1f} s"}
+        lines[f"{d}d"] = line
+        del a, b, off, obj, x, st
+        torch.cuda.empty_cache()
+    return lines
+
+
+def run_lp3d_only(args):
+    """--lp3d-only: three solves of the ragged 3-D batch, nothing else."""
+    import torch
+
+    from paper_1902_04995_gb300 import lp2d, workloads
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    b3 = workloads.ragged3d(seed=args.seed)
+    t3 = {k: torch.from_numpy(np.ascontiguousarray(b3[k]).reshape(-1)).to(dev)
+          for k in ("ax", "ay", "az", "b", "offsets", "obj")}
+    n3 = len(b3["offsets"]) - 1
+    opts = lp2d.default_options(seed=args.seed)
+    ws = lp2d.new_workspace(n3, opts, device=dev)
+    xyz = torch.empty(3 * n3, device=dev)
+    st3 = torch.empty(n3, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        lp2d.solve_batch3d(t3["ax"], t3["ay"], t3["az"], t3["b"], t3["offsets"], t3["obj"], b3["box"], xyz, st3,
+                           opts, ws)
+    torch.cuda.synchronize()
+    print(json.dumps({"lp3d_only": True, "n_lp": n3, "n_constraints": int(b3["offsets"][-1]),
+                      "status_counts": np.bincount(st3.cpu().numpy(), minlength=4).tolist()}), flush=True)
+
+
+def run_lpnd_only(args):
+    """--lpnd-only D: three solves of a d-dimensional ragged batch, nothing else."""
+    import torch
+
+    from paper_1902_04995_gb300 import lp2d, workloads
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    d = args.lpnd_only
+    bd = workloads.ragged_nd(d, seed=args.seed, n_lp=args.lpnd_lps)
+    a = torch.from_numpy(bd["a"]).to(dev)
+    b = torch.from_numpy(bd["b"]).to(dev)
+    off = torch.from_numpy(bd["offsets"]).to(dev)
+    obj = torch.from_numpy(bd["obj"].reshape(-1)).to(dev)
+    n = len(bd["offsets"]) - 1
+    opts = lp2d.default_options(seed=args.seed)
+    ws = lp2d.new_workspace(n, opts, device=dev)
+    x = torch.empty(d * n, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    lp2d.solve_batch_nd(a, b, off, obj, bd["box"], x, st, opts, ws)
+    e0.record()
+    for _ in range(2):
+        lp2d.solve_batch_nd(a, b, off, obj, bd["box"], x, st, opts, ws)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"lpnd_only": d, "n_lp": n, "n_constraints": int(bd["offsets"][-1]),
+                      "ms_per_solve": e0.elapsed_time(e1) / 2,
+                      "status_counts": np.bincount(st.cpu().numpy(), minlength=4).tolist()}), flush=True)
 
 
 def sample_batch3(batch, n_lp_sample):
@@ -491,6 +627,9 @@ def run_ours(args):
     lp3d_line = None
     if not args.no_lp3d:
         lp3d_line = measure_lp3d(args, dev, stream, measured_peaks()[0], world)
+    lpnd_lines = None
+    if not args.no_lpnd:
+        lpnd_lines = measure_lpnd(args, dev, stream, measured_peaks()[0], world)
 
     # ---- serving: Poisson requests (2,000/s) admitted under a 20 GB device cap
     serve_line = None
@@ -562,6 +701,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "serve": serve_line,
         "lp3d": lp3d_line,
+        "lpnd": lpnd_lines,
         "autotune": tune,
         "graph100_ms_per_solve": graph100_ms,
         "clocks": clocks,
@@ -577,6 +717,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.lpnd_only:
+        run_lpnd_only(args)
+    elif args.lp3d_only:
+        run_lp3d_only(args)
     else:
         run_ours(args)
 
