@@ -200,3 +200,49 @@ def test_results_identical_across_tuning_and_repeated_launches():
     torch.cuda.synchronize()
     assert (st.cpu().numpy() == base["status"]).all()
     assert np.array_equal(x.cpu().numpy().reshape(-1, d).astype(np.float64), base["x"], equal_nan=True)
+
+
+@pytest.mark.parametrize("prec", [lp2d.PREC_FP32, lp2d.PREC_FP64])
+@pytest.mark.parametrize("d", [4, 5])
+def test_degenerate_lifted_lps_match_the_oracle(d, prec):
+    # a (d-1)-dimensional batch with a zero last coefficient and a zero last objective
+    # entry: every optimum is a segment along the last axis (BOX_BOUNDED on both sides),
+    # box-vertex candidates are singular, and the objective must still match
+    low = workloads.ball_batch(d - 1, workloads.loguniform_sizes(np.random.default_rng(40 + d), 600, 1, 500),
+                               seed=41 + d, infeasible_frac=0.15)
+    n = low["a"].shape[1]
+    batch = {"a": np.vstack([low["a"], np.zeros((1, n), np.float32)]), "b": low["b"], "offsets": low["offsets"],
+             "obj": np.hstack([low["obj"], np.zeros((600, 1), np.float32)]),
+             "box": tuple(low["box"]) + (-7.0, 3.0)}
+    got = gpu_solve_nd(batch, seed=4, precision=prec)
+    ref = oracle_nd(batch, seed=4)
+    assert_parity(batch["obj"], got, ref, TOL[prec])
+    assert (got["status"][ref["status"] != oracle.INFEASIBLE] == oracle.BOX_BOUNDED).all()
+
+
+@pytest.mark.parametrize("d", [3, 4, 5])
+def test_duplicate_and_zero_normal_constraints_match_the_oracle(d):
+    rng = np.random.default_rng(50 + d)
+    base = workloads.ball_batch(d, np.full(300, 60), seed=51 + d, infeasible_frac=0.1)
+    a_parts, b_parts, sizes = [], [], []
+    for l in range(300):
+        s, e = base["offsets"][l], base["offsets"][l + 1]
+        a, b = base["a"][:, s:e], base["b"][s:e]
+        dup = rng.choice(e - s, size=10)  # exact copies of ten of its constraints
+        zero_b = np.where(np.arange(3) < 2, 1.0, -1.0 if l % 7 == 0 else 2.0).astype(np.float32)
+        a = np.hstack([a, a[:, dup], np.zeros((d, 3), np.float32)])
+        b = np.r_[b, b[dup], zero_b].astype(np.float32)
+        perm = rng.permutation(a.shape[1])
+        a_parts.append(a[:, perm])
+        b_parts.append(b[perm])
+        sizes.append(a.shape[1])
+    offsets = np.zeros(301, np.int64)
+    np.cumsum(sizes, out=offsets[1:])
+    batch = {"a": np.ascontiguousarray(np.hstack(a_parts)), "b": np.concatenate(b_parts), "offsets": offsets,
+             "obj": base["obj"], "box": base["box"]}
+    for prec in (lp2d.PREC_FP32, lp2d.PREC_FP64):
+        got = gpu_solve_nd(batch, seed=6, precision=prec)
+        ref = oracle_nd(batch, seed=6)
+        assert_parity(batch["obj"], got, ref, TOL[prec])
+    # 0.x <= -1 excludes everything: every seventh LP is infeasible
+    assert (ref["status"][::7] == oracle.INFEASIBLE).all()
