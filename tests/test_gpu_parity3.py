@@ -212,3 +212,40 @@ def test_least_violation_in_fp64():
         # |a| as the least-violation LP defines it (float32)
         viol = (a @ got_xy[l] - batch["b"][s0:e0]) / -lv["az"][s0:e0].astype(np.float64)
         assert viol.max() <= ref["xyz"][l, 2] + 1e-9
+
+
+@pytest.mark.parametrize("prec", [lp2d.PREC_FP32, lp2d.PREC_FP64])
+def test_degenerate_lifted_and_duplicate_constraints(prec):
+    # 2-D LPs lifted to 3-D (az = 0, c_z = 0): every optimum is a segment along z,
+    # BOX_BOUNDED on both sides; then exact duplicates and zero-normal constraints
+    rng = np.random.default_rng(61)
+    low = workloads.disk_batch(workloads.loguniform_sizes(rng, 800, 1, 500), seed=62, infeasible_frac=0.15)
+    n = low["ax"].shape[0]
+    lifted = {"ax": low["ax"], "ay": low["ay"], "az": np.zeros(n, np.float32), "b": low["b"],
+              "offsets": low["offsets"], "obj": np.hstack([low["obj"], np.zeros((800, 1), np.float32)]),
+              "box": tuple(low["box"]) + (-7.0, 3.0)}
+    got = gpu_solve3(lifted, seed=2, precision=prec)
+    ref = oracle3(lifted, seed=2)
+    assert_parity3(lifted, got, ref, TOL[prec])
+    assert (got["status"][ref["status"] != oracle.INFEASIBLE] == oracle.BOX_BOUNDED).all()
+    base = workloads.sphere_batch(np.full(300, 60), seed=63, infeasible_frac=0.1)
+    cols = {k: [] for k in ("ax", "ay", "az", "b")}
+    sizes = []
+    for l in range(300):
+        s, e = base["offsets"][l], base["offsets"][l + 1]
+        dup = rng.choice(e - s, size=10)
+        extra_b = np.array([1.0, 1.0, -1.0 if l % 7 == 0 else 2.0], np.float32)
+        perm = rng.permutation(e - s + 13)
+        for k in ("ax", "ay", "az"):
+            v = base[k][s:e]
+            cols[k].append(np.r_[v, v[dup], np.zeros(3, np.float32)][perm])
+        cols["b"].append(np.r_[base["b"][s:e], base["b"][s:e][dup], extra_b][perm].astype(np.float32))
+        sizes.append(e - s + 13)
+    offsets = np.zeros(301, np.int64)
+    np.cumsum(sizes, out=offsets[1:])
+    batch = {k: np.concatenate(v).astype(np.float32) for k, v in cols.items()}
+    batch.update({"offsets": offsets, "obj": base["obj"], "box": base["box"]})
+    got = gpu_solve3(batch, seed=3, precision=prec)
+    ref = oracle3(batch, seed=3)
+    assert_parity3(batch, got, ref, TOL[prec])
+    assert (ref["status"][::7] == oracle.INFEASIBLE).all()
