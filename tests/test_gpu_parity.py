@@ -349,3 +349,58 @@ def test_mixed_precision_needs_persistent_schedule():
     with pytest.raises(lp2d.LP2DError) as e:
         gpu_solve(batch, precision=lp2d.PREC_FP32_F64ISECT, schedule=lp2d.SCHED_UNIFORM)
     assert e.value.code == lp2d.ERR_UNSUPPORTED
+
+
+# --------------------------------------------------------- degenerate inputs
+@pytest.mark.parametrize("prec,sched", [(lp2d.PREC_FP32, lp2d.SCHED_PERSISTENT), (lp2d.PREC_FP64, lp2d.SCHED_PERSISTENT),
+                                        (lp2d.PREC_FP32_F64ISECT, lp2d.SCHED_PERSISTENT),
+                                        (lp2d.PREC_FP64, lp2d.SCHED_UNIFORM)])
+def test_degenerate_lifted_duplicate_and_zero_normal_constraints(prec, sched):
+    """1-D LPs lifted to 2-D (a_y = 0, c_y = 0: segment optima, BOX_BOUNDED), then LPs
+    with exact duplicate and zero-normal constraints; status exact, objective within
+    the mode's tolerance (the vertex of a segment optimum is not unique)."""
+    rng = np.random.default_rng(71)
+    tol = 1e-10 if prec == lp2d.PREC_FP64 else 1e-4
+
+    def check(batch, seed):
+        got = gpu_solve(batch, seed=seed, precision=prec, schedule=sched)
+        ref = oracle_solve(batch, seed=seed)
+        assert np.array_equal(got["status"], ref["status"]), np.nonzero(got["status"] != ref["status"])[0][:8]
+        c = np.asarray(batch["obj"], np.float64).reshape(-1, 2)
+        ok = ref["status"] != oracle.INFEASIBLE
+        f_ref = np.einsum("ij,ij->i", ref["xy"][ok], c[ok])
+        f_got = np.einsum("ij,ij->i", got["xy"][ok], c[ok])
+        assert (np.abs(f_got - f_ref) / np.maximum(np.abs(f_ref), 1.0)).max(initial=0.0) <= tol
+        assert np.isnan(got["xy"][~ok]).all()
+        return ref
+
+    sizes = workloads.loguniform_sizes(rng, 800, 1, 1500)
+    offsets = np.zeros(801, np.int64)
+    np.cumsum(sizes, out=offsets[1:])
+    n = int(offsets[-1])
+    sgn = np.where(rng.random(n) < 0.5, -1.0, 1.0).astype(np.float32)
+    lifted = {"ax": sgn, "ay": np.zeros(n, np.float32), "b": rng.uniform(0.5, 3.0, n).astype(np.float32),
+              "offsets": offsets,
+              "obj": np.stack([np.where(rng.random(800) < 0.5, -1.0, 1.0), np.zeros(800)], 1).astype(np.float32),
+              "box": (-1e3, 1e3, -7.0, 3.0)}
+    ref = check(lifted, 2)
+    assert (ref["status"] == oracle.BOX_BOUNDED).all()
+    base = workloads.disk_batch(np.full(300, 60), seed=72, infeasible_frac=0.1)
+    cols = {k: [] for k in ("ax", "ay", "b")}
+    sz = []
+    for l in range(300):
+        s, e = base["offsets"][l], base["offsets"][l + 1]
+        dup = rng.choice(e - s, size=10)
+        extra_b = np.array([1.0, 1.0, -1.0 if l % 7 == 0 else 2.0], np.float32)
+        perm = rng.permutation(e - s + 13)
+        for k in ("ax", "ay"):
+            v = base[k][s:e]
+            cols[k].append(np.r_[v, v[dup], np.zeros(3, np.float32)][perm])
+        cols["b"].append(np.r_[base["b"][s:e], base["b"][s:e][dup], extra_b][perm].astype(np.float32))
+        sz.append(e - s + 13)
+    off2 = np.zeros(301, np.int64)
+    np.cumsum(sz, out=off2[1:])
+    batch = {k: np.concatenate(v).astype(np.float32) for k, v in cols.items()}
+    batch.update({"offsets": off2, "obj": base["obj"], "box": base["box"]})
+    ref = check(batch, 3)
+    assert (ref["status"][::7] == oracle.INFEASIBLE).all()
