@@ -49,7 +49,12 @@ def _load():
     if _lib is not None:
         return _lib
     build()
-    lib = ctypes.CDLL(_LIB_PATH)
+    _lib = _bind(ctypes.CDLL(_LIB_PATH))
+    return _lib
+
+
+def _bind(lib):
+    """Declare the C functions' signatures on a loaded copy of the oracle library."""
     u64, i64, i32, u32, dbl = ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_double
     vp = ctypes.c_void_p
     lib.oracle_splitmix64.restype = u64
@@ -68,7 +73,6 @@ def _load():
     lib.oracle_solve_batch3.argtypes = [vp, vp, vp, vp, vp, i64, i64, vp, vp, u64, dbl, vp, vp, vp, vp]
     lib.oracle_solve_batchN.restype = None
     lib.oracle_solve_batchN.argtypes = [ctypes.c_int, vp, vp, vp, i64, i64, vp, vp, u64, dbl, vp, vp, vp, vp]
-    _lib = lib
     return lib
 
 
