@@ -68,7 +68,8 @@ typedef enum {
 /** Bits of the device error word kept in the workspace. */
 enum {
     LP2D_DEVERR_BAD_OFFSETS = 1, /**< an LP had a negative size (status BAD_INPUT) */
-    LP2D_DEVERR_TOO_LARGE = 4    /**< a 3-D LP had more than LP3D_MAX_CONSTRAINTS constraints (BAD_INPUT) */
+    LP2D_DEVERR_TOO_LARGE = 4    /**< a 3-D LP had more than LP3D_MAX_CONSTRAINTS constraints, or a
+                                      d-dimensional one more than LPND_MAX_CONSTRAINTS(d) (BAD_INPUT) */
 };
 
 /** The bounding box: the +-M constraints of Sec. 2.1 (xmin < xmax, ymin < ymax, finite). */
