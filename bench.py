@@ -191,7 +191,7 @@ def sample_batch(batch, n_lp_sample):
             "obj": batch["obj"][:n_lp_sample], "box": batch["box"]}
 
 
-def measure_lp3d(args, dev, stream, peak, world):
+def measure_lp3d(args, dev, stream, peak, world, rank=0):
     """The batched 3-D solver on the 65,536-LP ragged 3-D batch (CUDA events over
     repeated launches; inputs 219 MB > L2) and the least-violation fallback on the
     infeasible LPs of a 2-D ragged batch of at most 1018 constraints per LP."""
@@ -200,7 +200,7 @@ def measure_lp3d(args, dev, stream, peak, world):
     from paper_1902_04995_gb300 import dist as lpdist
     from paper_1902_04995_gb300 import lp2d, workloads
 
-    b3 = workloads.ragged3d(seed=args.seed)
+    b3 = workloads.ragged3d(seed=args.seed + rank)  # every rank its own batch
     t3 = {k: torch.from_numpy(np.ascontiguousarray(b3[k]).reshape(-1)).to(dev)
           for k in ("ax", "ay", "az", "b", "offsets", "obj")}
     n3 = len(b3["offsets"]) - 1
@@ -230,7 +230,7 @@ def measure_lp3d(args, dev, stream, peak, world):
     algo3 = workloads.algorithmic_bytes(b3)
     status3 = np.bincount(st3.cpu().numpy(), minlength=4).tolist()
     # least violation: 2-D ragged batch capped at the 3-D solver's size limit
-    b2 = workloads.ragged(seed=args.seed, hi=1017)
+    b2 = workloads.ragged(seed=args.seed + rank, hi=1017)
     t2 = {k: torch.from_numpy(np.ascontiguousarray(b2[k]).reshape(-1)).to(dev) for k in ("ax", "ay", "b", "offsets", "obj")}
     n2 = len(b2["offsets"]) - 1
     xy = torch.empty(2 * n2, device=dev)
@@ -280,7 +280,7 @@ def measure_lp3d(args, dev, stream, peak, world):
     return line
 
 
-def measure_lpnd(args, dev, stream, peak, world, dims=(4, 5)):
+def measure_lpnd(args, dev, stream, peak, world, rank=0, dims=(4, 5)):
     """The batched d-dimensional solver on the 65,536-LP ragged ball batches of
     dimension 4 and 5 (CUDA events over repeated launches; inputs 273 / 329 MB > L2),
     each with the d-dimensional FP64 oracle on a bounded sample of its LPs."""
@@ -291,7 +291,7 @@ def measure_lpnd(args, dev, stream, peak, world, dims=(4, 5)):
 
     lines = {}
     for d in dims:
-        bd = workloads.ragged_nd(d, seed=args.seed)
+        bd = workloads.ragged_nd(d, seed=args.seed + rank)  # every rank its own batch
         a = torch.from_numpy(bd["a"]).to(dev)
         b = torch.from_numpy(bd["b"]).to(dev)
         off = torch.from_numpy(bd["offsets"]).to(dev)
@@ -626,10 +626,10 @@ def run_ours(args):
     # ---- the 3-D solver and the least-violation fallback (widened rows of the method)
     lp3d_line = None
     if not args.no_lp3d:
-        lp3d_line = measure_lp3d(args, dev, stream, measured_peaks()[0], world)
+        lp3d_line = measure_lp3d(args, dev, stream, measured_peaks()[0], world, rank)
     lpnd_lines = None
     if not args.no_lpnd:
-        lpnd_lines = measure_lpnd(args, dev, stream, measured_peaks()[0], world)
+        lpnd_lines = measure_lpnd(args, dev, stream, measured_peaks()[0], world, rank)
 
     # ---- serving: Poisson requests (2,000/s) admitted under a 20 GB device cap
     serve_line = None
