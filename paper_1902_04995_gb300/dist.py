@@ -39,12 +39,18 @@ def shard_lp_range(offsets, rank: int, world: int):
 
 def slice_batch(batch, lo: int, hi: int, seed: int = 0):
     """LPs lo..hi-1 of a batch as a batch of their own (views into the arrays,
-    offsets rebased to 0), and the seed that keeps their visit orders unchanged."""
+    offsets rebased to 0), and the seed that keeps their visit orders unchanged.
+    Works for 2-D (ax, ay, b), 3-D (ax, ay, az, b) and d-dimensional (a [d, n], b)
+    batches."""
     off = batch["offsets"]
     s, e = int(off[lo]), int(off[hi])
     sub = dict(batch)
-    sub.update({"ax": batch["ax"][s:e], "ay": batch["ay"][s:e], "b": batch["b"][s:e],
-                "offsets": off[lo:hi + 1] - s, "obj": batch["obj"][lo:hi]})
+    for key in ("ax", "ay", "az", "b"):
+        if key in batch:
+            sub[key] = batch[key][s:e]
+    if "a" in batch:
+        sub["a"] = batch["a"][:, s:e]
+    sub.update({"offsets": off[lo:hi + 1] - s, "obj": batch["obj"][lo:hi]})
     if "infeasible" in batch:
         sub["infeasible"] = batch["infeasible"][lo:hi]
     return sub, seed + lo
