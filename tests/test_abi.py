@@ -211,3 +211,18 @@ def test_product_path_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "seidel_oracle" not in text, f
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    # a copy of the package without liblp2d.so: importing the binding must raise, never
+    # fall back to anything else
+    import shutil
+    import subprocess
+    import sys
+
+    shutil.copytree(os.path.join(ROOT, "paper_1902_04995_gb300"), tmp_path / "paper_1902_04995_gb300",
+                    ignore=shutil.ignore_patterns("*.so", "_build", "__pycache__"))
+    r = subprocess.run([sys.executable, "-c", "import paper_1902_04995_gb300.lp2d"], cwd=tmp_path,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "is missing" in r.stderr
