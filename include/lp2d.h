@@ -111,6 +111,13 @@ typedef struct {
                                  through the returned vertex (>= 0: the LP's own constraint
                                  index; -1..-4: box side x<=xmax, x>=xmin, y<=ymax, y>=ymin).
                                  Undefined for INFEASIBLE / BAD_INPUT LPs. */
+    int32_t team_min_slots; /**< persistent schedule: a 1-D LP of a large LP (more than 1024
+                                 constraints) over at least this many earlier constraints (box
+                                 included) is shared by the CTA's 128 threads, a shorter one runs
+                                 on the driving warp's 32 (64..4096; 0 = default 1024) */
+    int32_t l2_prefetch;    /**< persistent schedule: 0 or 1 = bulk-prefetch the constraints of
+                                 every LP a CTA or warp takes from the queue into L2 (default);
+                                 -1 = no prefetch */
 } lp2d_options;
 
 /** Fill *opt with the defaults listed above. */

@@ -96,6 +96,8 @@ void lp2d_default_options(lp2d_options* opt) {
     opt->near_parallel_tau = 0.0f;
     opt->out_nviol = nullptr;
     opt->out_def = nullptr;
+    opt->team_min_slots = 0;
+    opt->l2_prefetch = 0;
 }
 
 size_t lp2d_workspace_bytes(int64_t n_lp, const lp2d_options* opt) {
@@ -127,6 +129,11 @@ int lp2d_solve_batch_ex(const float* ax, const float* ay, const float* b, const 
         return fail(LP2D_ERR_INVALID_ARGUMENT, "unknown schedule %d", opt.schedule);
     if (opt.ctas_per_sm < 0 || opt.chunk_big < 0 || opt.chunk_small < 0)
         return fail(LP2D_ERR_INVALID_ARGUMENT, "negative tuning parameter");
+    if (opt.team_min_slots != 0 && (opt.team_min_slots < 64 || opt.team_min_slots > 4096))
+        return fail(LP2D_ERR_INVALID_ARGUMENT, "team_min_slots = %d outside 64..4096 (0 = default)",
+                    opt.team_min_slots);
+    if (opt.l2_prefetch < -1 || opt.l2_prefetch > 1)
+        return fail(LP2D_ERR_INVALID_ARGUMENT, "l2_prefetch = %d is not -1, 0 or 1", opt.l2_prefetch);
     if (!(opt.eps >= 0.0f) || !finite(opt.eps) || !(opt.near_parallel_tau >= 0.0f) || !finite(opt.near_parallel_tau))
         return fail(LP2D_ERR_INVALID_ARGUMENT, "eps / near_parallel_tau must be finite and >= 0");
     if (!finite(box.xmin) || !finite(box.xmax) || !finite(box.ymin) || !finite(box.ymax) ||
@@ -180,6 +187,8 @@ int lp2d_solve_batch_ex(const float* ax, const float* ay, const float* b, const 
                         ? (opt.chunk_small < lp2d::kMaxChunkSmall ? opt.chunk_small : lp2d::kMaxChunkSmall)
                         : lp2d::kDefaultChunkSmall;
     p.check_finite = opt.check_finite ? 1 : 0;
+    p.team_min = opt.team_min_slots > 0 ? opt.team_min_slots : lp2d::kDefaultTeamMin;
+    p.prefetch = opt.l2_prefetch > 0 ? 1 : 0;
 
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const bool fp64 = opt.precision == LP2D_PREC_FP64;

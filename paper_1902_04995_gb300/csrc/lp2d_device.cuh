@@ -50,6 +50,8 @@ struct Params {
     int chunk_big;
     int chunk_small;
     int check_finite;
+    int team_min;   // 1-D LPs over at least this many stage slots get the CTA's helper warps
+    int prefetch;   // non-zero: bulk-prefetch each grabbed LP's constraints into L2
 };
 
 // ------------------------------------------------------------------ visit order

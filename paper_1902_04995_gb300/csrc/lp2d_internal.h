@@ -10,9 +10,11 @@ namespace lp2d {
 // Shapes of the persistent schedule (see lp2d_persistent.cu).
 constexpr int kPersistentWarps = 4;   // warps per CTA
 constexpr int kPersistentMinCtas = 8; // resident CTAs per SM the FP32 register budget is fitted to
-constexpr int kCapSmall = 508;        // largest LP one warp stages (512 slots with the box)
-constexpr int kCapMid = 1020;         // largest LP one warp stages in half a CTA stage (1024 slots)
-constexpr int kCapBig = 2044;         // largest LP a CTA stages (2048 slots with the box)
+constexpr int kStageSlots = 2064;     // stage slots per CTA (8 B + 4 B each)
+constexpr int kCapSmall = 512;        // largest LP one warp stages in a quarter of the stage (516 slots)
+constexpr int kCapMid = 1024;         // largest LP one warp stages in half of the stage (its keys fit 32 words)
+constexpr int kCapBig = 2060;         // largest LP the CTA stages (the box and 2060 constraints)
+constexpr int kDefaultTeamMin = 1024; // 1-D LPs over at least this many slots get the helper warps
 constexpr int kMaxChunk = 32;         // LP indices per queue grab, at most
 constexpr int kMaxChunkSmall = 16;    // largest target of LPs per warp grab
 constexpr int kDefaultChunkBig = 1;   // target large LPs per CTA grab

@@ -18,16 +18,33 @@
 // the same stream without a memset.
 #include "lp2d_internal.h"
 #include "lp2d_solve.cuh"
-#include "lp2d_staged.cuh"
+#include "lp2d_warp.cuh"
 
 namespace lp2d {
 
-constexpr int kWarpSlots = kCapSmall + kBoxSlots;                // stage slots per warp
-constexpr int kStageSlots = kPersistentWarps * kWarpSlots;      // stage slots per CTA
-static_assert(kStageSlots - kBoxSlots == kCapBig, "team capacity");
-constexpr int kMidWarps = 2;                                    // warps with half a stage each
-constexpr int kMidSlots = kStageSlots / kMidWarps;              // their stage slots
-static_assert(kMidSlots - kBoxSlots == kCapMid && kMidSlots <= 1024, "half-stage capacity (warp bitmap)");
+constexpr int kWarpSlots = kStageSlots / kPersistentWarps;  // stage slots per warp (phase 3)
+constexpr int kMidWarps = 2;                                // warps with half a stage each (phase 2)
+constexpr int kMidSlots = kStageSlots / kMidWarps;          // their stage slots
+static_assert(kWarpSlots - kBoxSlots >= kCapSmall, "quarter-stage capacity");
+static_assert(kMidSlots - kBoxSlots >= kCapMid && kCapMid <= 1024, "half-stage capacity (32-word key bitmap)");
+static_assert(kStageSlots - kBoxSlots >= kCapBig && kCapBig <= 4096, "stage capacity (128-word key bitmap)");
+// Keys a thread keeps in registers between the staging passes (two per register):
+// LPs of up to 128 constraints on a warp and every CTA-staged LP keep them; the
+// staging of other warp LPs computes them again (fewer registers and less code).
+constexpr int kKeysSmall = 4;
+constexpr int kKeysMid = 0;
+constexpr int kKeysBig = (kCapBig + 127) / 128;
+
+// The FP32 iterations have their own driver; the other precisions share drive_lp2.
+template <typename Real, bool kMixed, bool kTeam>
+__device__ __forceinline__ void drive(const Params& P, int64_t lp, int m, float cx, float cy, const VisitOrder& vo,
+                                      const float2* sA, const float* sB, const unsigned* bm, int lane,
+                                      TeamJob2<Real>* job) {
+    if constexpr (sizeof(Real) == 4 && !kMixed)
+        drive_f32<kTeam>(P, lp, m, cx, cy, vo, sA, sB, bm, lane, job);
+    else
+        drive_lp2<Real, kMixed, kTeam>(P, lp, m, cx, cy, vo, sA, sB, bm, lane, job);
+}
 
 template <typename Real>
 __device__ __forceinline__ void write_bad(const Params& P, int64_t lp) {
@@ -48,31 +65,43 @@ __device__ __forceinline__ int next_span(int span, int found, int target) {
 }
 
 // A warp's next grab from the queue at *head: `span` LP indices starting at the
-// returned index; lane l < span gets the first offset and the size of LP start + l.
-// The caller picks its LPs out of the grab by ballot.
+// returned index; lane l < span gets the first offset, the size and the objective of
+// LP start + l.  The caller picks its LPs out of the grab by ballot.
 __device__ __forceinline__ long long warp_grab(const Params& P, unsigned long long* head, int span, int lane,
-                                               long long& off_l, long long& mm_l) {
+                                               long long& off_l, long long& mm_l, float& cx_l, float& cy_l) {
     long long start = 0;
     if (lane == 0) start = static_cast<long long>(atomicAdd(head, static_cast<unsigned long long>(span)));
     start = __shfl_sync(kFull, start, 0);
     off_l = 0;
     mm_l = 0;
+    cx_l = cy_l = 0.0f;
     if (start >= 0 && start < P.n_lp && lane < span && start + lane < P.n_lp) {
         off_l = __ldg(P.offsets + start + lane);
         mm_l = __ldg(P.offsets + start + lane + 1) - off_l;
+        cx_l = __ldg(P.obj + 2 * (start + lane));
+        cy_l = __ldg(P.obj + 2 * (start + lane) + 1);
     }
     return start;
 }
 
+// Lanes whose bit is set in `todo` prefetch their LP's constraint segments into L2.
+__device__ __forceinline__ void prefetch_grab(const Params& P, unsigned todo, long long off_l, long long mm_l,
+                                              int lane) {
+    if (P.prefetch && ((todo >> lane) & 1u)) {
+        prefetch_l2(P.ax + off_l, mm_l);
+        prefetch_l2(P.ay + off_l, mm_l);
+        prefetch_l2(P.b + off_l, mm_l);
+    }
+}
+
 template <typename Real, bool kMixed>
 __device__ __forceinline__ void persistent_body(const Params& P) {
-    __shared__ float sX[kStageSlots];
-    __shared__ float sY[kStageSlots];
+    __shared__ float2 sA[kStageSlots];
     __shared__ float sB[kStageSlots];
     __shared__ unsigned s_bm[kPersistentWarps * 32];  // key bitmaps (32 words per warp, 128 per CTA)
-    __shared__ int s_pre[kPersistentWarps * 32];      // their prefix counts (CTA staging)
+    __shared__ int s_pre[kPersistentWarps * 32];      // their prefix counts
     __shared__ int s_wsum[kPersistentWarps];
-    __shared__ TeamJob job;
+    __shared__ TeamJob2<Real> job;
     __shared__ TeamScratch<kPersistentWarps> sc;  // the read-from-HBM path
     __shared__ long long s_grab;
     __shared__ long long s_off[kMaxChunk + 1];
@@ -85,6 +114,7 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
     unsigned long long* ws = P.ws;
 
     // ---- phase 1: large LPs, one CTA each (grab spans adapt as in next_span)
+    if (warp == 0) write_box2(P, sA, sB, lane);  // slots 0..3 stay the box for the whole phase
     int big_span = P.chunk_big;
     for (;;) {
         __syncthreads();  // the previous chunk's s_grab / s_off / stage are no longer read
@@ -96,6 +126,14 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
         if (tid <= cnt) s_off[tid] = __ldg(P.offsets + start + tid);
         if (tid < 2 * cnt) s_obj[tid] = __ldg(P.obj + 2 * start + tid);
         __syncthreads();
+        if (P.prefetch && tid < cnt) {
+            const long long o = s_off[tid], n = s_off[tid + 1] - o;
+            if (n > kCapMid && n <= kCapBig) {
+                prefetch_l2(P.ax + o, n);
+                prefetch_l2(P.ay + o, n);
+                prefetch_l2(P.b + o, n);
+            }
+        }
         int found = 0;
         for (int i = 0; i < cnt; ++i) {
             const int64_t lp = start + i;
@@ -114,14 +152,13 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
             }
             VisitOrder vo;
             warp_visit_order(vo, P.seed + static_cast<uint64_t>(lp), static_cast<uint32_t>(m), lane);
-            if (warp == 0) write_box(P, sX, sY, sB, lane);
-            stage_lp_team(vo, m, P.ax + base, P.ay + base, P.b + base, sX, sY, sB, s_bm, s_pre, s_wsum, tid);
+            stage_lp2<128, kKeysBig>(vo, m, P.ax + base, P.ay + base, P.b + base, sA, sB, s_bm, s_pre, s_wsum, tid);
             cp_async_wait_all();
             __syncthreads();
             if (warp == 0)
-                drive_lp<Real, kMixed, true>(P, lp, m, s_obj[2 * i], s_obj[2 * i + 1], vo, sX, sY, sB, s_bm, lane, &job);
+                drive<Real, kMixed, true>(P, lp, m, s_obj[2 * i], s_obj[2 * i + 1], vo, sA, sB, s_bm, lane, &job);
             else
-                team_helper<Real, kMixed>(sX, sY, sB, &job, tid);
+                team_helper2<Real, kMixed>(sA, sB, &job, tid);
             __syncthreads();
         }
         big_span = next_span(big_span, found, P.chunk_big);
@@ -129,31 +166,33 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
 
     // ---- phase 2: mid-size LPs, one warp each for warps 0 and 1 (half a stage each)
     if (warp < kMidWarps) {
-        float* hX = sX + warp * kMidSlots;
-        float* hY = sY + warp * kMidSlots;
+        float2* hA = sA + warp * kMidSlots;
         float* hB = sB + warp * kMidSlots;
         unsigned* hbm = s_bm + warp * 32;
+        int* hpre = s_pre + warp * 32;
+        write_box2(P, hA, hB, lane);
         int span = P.chunk_small;
         for (;;) {
             long long off_l, mm_l;
-            const long long start = warp_grab(P, ws + kWsHeadMid, span, lane, off_l, mm_l);
+            float cx_l, cy_l;
+            const long long start = warp_grab(P, ws + kWsHeadMid, span, lane, off_l, mm_l, cx_l, cy_l);
             if (start < 0 || start >= P.n_lp) break;
             unsigned todo = __ballot_sync(kFull, lane < span && mm_l > kCapSmall && mm_l <= kCapMid);
             span = next_span(span, __popc(todo), P.chunk_small);
+            prefetch_grab(P, todo, off_l, mm_l, lane);
             while (todo != 0u) {
                 const int i = __ffs(todo) - 1;
                 todo &= todo - 1u;
                 const int64_t lp = start + i;
                 const int64_t base = __shfl_sync(kFull, off_l, i);
                 const int m = static_cast<int>(__shfl_sync(kFull, mm_l, i));
-                const float cx = __ldg(P.obj + 2 * lp), cy = __ldg(P.obj + 2 * lp + 1);
+                const float cx = __shfl_sync(kFull, cx_l, i), cy = __shfl_sync(kFull, cy_l, i);
                 VisitOrder vo;
                 warp_visit_order(vo, P.seed + static_cast<uint64_t>(lp), static_cast<uint32_t>(m), lane);
-                write_box(P, hX, hY, hB, lane);
-                stage_lp_warp(vo, m, P.ax + base, P.ay + base, P.b + base, hX, hY, hB, hbm, lane);
+                stage_lp2<32, kKeysMid>(vo, m, P.ax + base, P.ay + base, P.b + base, hA, hB, hbm, hpre, nullptr, lane);
                 cp_async_wait_all();
                 __syncwarp();
-                drive_lp<Real, kMixed, false>(P, lp, m, cx, cy, vo, hX, hY, hB, hbm, lane, nullptr);
+                drive<Real, kMixed, false>(P, lp, m, cx, cy, vo, hA, hB, hbm, lane, nullptr);
                 __syncwarp();  // all lanes are done with the stage before it is overwritten
             }
         }
@@ -161,18 +200,21 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
     __syncthreads();  // the half stages are free for phase 3
 
     // ---- phase 3: small LPs, one warp each
-    float* wX = sX + warp * kWarpSlots;
-    float* wY = sY + warp * kWarpSlots;
+    float2* wA = sA + warp * kWarpSlots;
     float* wB = sB + warp * kWarpSlots;
     unsigned* wbm = s_bm + warp * 32;
+    int* wpre = s_pre + warp * 32;
+    write_box2(P, wA, wB, lane);
     int span = P.chunk_small;
     for (;;) {
         long long off_l, mm_l;
-        const long long start = warp_grab(P, ws + kWsHeadSmall, span, lane, off_l, mm_l);
+        float cx_l, cy_l;
+        const long long start = warp_grab(P, ws + kWsHeadSmall, span, lane, off_l, mm_l, cx_l, cy_l);
         if (start < 0 || start >= P.n_lp) break;
         // negative sizes (bad offsets) are reported here
         unsigned todo = __ballot_sync(kFull, lane < span && start + lane < P.n_lp && mm_l <= kCapSmall);
         span = next_span(span, __popc(todo), P.chunk_small);
+        prefetch_grab(P, todo, off_l, mm_l, lane);
         while (todo != 0u) {
             const int i = __ffs(todo) - 1;
             todo &= todo - 1u;
@@ -184,14 +226,13 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
                 continue;
             }
             const int m = static_cast<int>(mm);
-            const float cx = __ldg(P.obj + 2 * lp), cy = __ldg(P.obj + 2 * lp + 1);
+            const float cx = __shfl_sync(kFull, cx_l, i), cy = __shfl_sync(kFull, cy_l, i);
             VisitOrder vo;
             warp_visit_order(vo, P.seed + static_cast<uint64_t>(lp), static_cast<uint32_t>(m), lane);
-            write_box(P, wX, wY, wB, lane);
-            stage_lp_warp(vo, m, P.ax + base, P.ay + base, P.b + base, wX, wY, wB, wbm, lane);
+            stage_lp2<32, kKeysSmall>(vo, m, P.ax + base, P.ay + base, P.b + base, wA, wB, wbm, wpre, nullptr, lane);
             cp_async_wait_all();
             __syncwarp();
-            drive_lp<Real, kMixed, false>(P, lp, m, cx, cy, vo, wX, wY, wB, wbm, lane, nullptr);
+            drive<Real, kMixed, false>(P, lp, m, cx, cy, vo, wA, wB, wbm, lane, nullptr);
             __syncwarp();  // all lanes are done with the stage before it is overwritten
         }
     }
@@ -210,11 +251,12 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
     }
 }
 
-// The plain kernels keep the compiler's register choice; the mixed-precision one,
-// whose cold FP64 path would otherwise raise the register count, is fitted to
-// kPersistentMinCtas resident CTAs per SM.
+// The FP32 kernels are fitted to kPersistentMinCtas resident CTAs per SM (the shared
+// memory of a CTA allows that many; registers must not take one away); the FP64 one
+// keeps the compiler's register choice.
 template <typename Real>
-__global__ void __launch_bounds__(kPersistentWarps * 32) seidel_persistent_kernel(const Params P) {
+__global__ void __launch_bounds__(kPersistentWarps * 32, sizeof(Real) == 4 ? kPersistentMinCtas : 1)
+seidel_persistent_kernel(const Params P) {
     persistent_body<Real, false>(P);
 }
 

@@ -41,6 +41,8 @@ class Options(ctypes.Structure):
         ("near_parallel_tau", ctypes.c_float),
         ("out_nviol", ctypes.c_void_p),
         ("out_def", ctypes.c_void_p),
+        ("team_min_slots", ctypes.c_int32),
+        ("l2_prefetch", ctypes.c_int32),
     ]
 
 

@@ -167,13 +167,14 @@ def test_results_identical_across_tuning():
     batch = workloads.ragged(n_lp=20000)
     base = gpu_solve(batch, seed=2)
     for tune in ({"ctas_per_sm": 1}, {"ctas_per_sm": 3, "chunk_big": 1, "chunk_small": 1},
-                 {"chunk_big": 16, "chunk_small": 8}):
+                 {"chunk_big": 16, "chunk_small": 8}, {"team_min_slots": 64}, {"team_min_slots": 4096},
+                 {"l2_prefetch": -1, "team_min_slots": 300}):
         got = gpu_solve(batch, seed=2, **tune)
         assert (got["status"] == base["status"]).all()
         assert np.array_equal(got["xy"], base["xy"], equal_nan=True), tune
 
 
-@pytest.mark.parametrize("lo,hi,n_lp", [(8, 16, 20000), (509, 1020, 3000), (1021, 2044, 2000), (1, 8, 30000)])
+@pytest.mark.parametrize("lo,hi,n_lp", [(8, 16, 20000), (513, 1024, 3000), (1025, 2060, 2000), (1, 8, 30000)])
 def test_batches_of_one_size_class(lo, hi, n_lp):
     # every LP in one size class: the queue of that class is dense and the others are
     # empty, so each phase's grab spans take their extreme values
@@ -235,10 +236,11 @@ def test_repeated_launches_reuse_workspace_and_graph_replay_is_identical():
 
 # ----------------------------------------------------------- edge cases
 def test_ragged_edges_tiles_and_tails():
-    # sizes straddling the warp (32), team (128), per-warp stage (512) and CTA stage
-    # (2048) boundaries, plus LPs beyond the stage that read through pi from HBM.
-    sizes = np.array([0, 1, 2, 3, 4, 31, 32, 33, 63, 64, 65, 127, 128, 129, 511, 512, 513, 2047, 2048, 2049,
-                      3000, 9000], dtype=np.int64)
+    # sizes straddling the warp (32), team (128), quarter-stage (512), half-stage (1024)
+    # and CTA-stage (2060) boundaries, plus LPs beyond the stage that read through pi
+    # from HBM.
+    sizes = np.array([0, 1, 2, 3, 4, 31, 32, 33, 63, 64, 65, 127, 128, 129, 511, 512, 513, 1023, 1024, 1025,
+                      2047, 2048, 2049, 2059, 2060, 2061, 3000, 9000], dtype=np.int64)
     sizes = np.concatenate([sizes, sizes[::-1], sizes])
     batch = workloads.disk_batch(sizes, seed=4, infeasible_frac=0.3)
     for prec in (lp2d.PREC_FP32, lp2d.PREC_FP64):
