@@ -29,11 +29,16 @@ static_assert(kWarpSlots - kBoxSlots >= kCapSmall, "quarter-stage capacity");
 static_assert(kMidSlots - kBoxSlots >= kCapMid && kCapMid <= 1024, "half-stage capacity (32-word key bitmap)");
 static_assert(kStageSlots - kBoxSlots >= kCapBig && kCapBig <= 4096, "stage capacity (128-word key bitmap)");
 // Keys a thread keeps in registers between the staging passes (two per register):
-// LPs of up to 128 constraints on a warp and every CTA-staged LP keep them; the
-// staging of other warp LPs computes them again (fewer registers and less code).
-constexpr int kKeysSmall = 4;
+// quarter-stage and CTA-staged LPs keep them; a half-stage LP computes them again
+// (fewer registers and less code).
+constexpr int kKeysSmall = (kCapSmall + 31) / 32;
 constexpr int kKeysMid = 0;
 constexpr int kKeysBig = (kCapBig + 127) / 128;
+
+// Rows of 32 positions the FP32 driver tests per step: large LPs, warp LPs.
+constexpr int kRowsBig = 2;
+constexpr int kRowsWarp = 1;
+constexpr bool kAheadBig = true;  // large LPs: load the next window one step ahead
 
 // The FP32 iterations have their own driver; the other precisions share drive_lp2.
 template <typename Real, bool kMixed, bool kTeam>
@@ -41,7 +46,8 @@ __device__ __forceinline__ void drive(const Params& P, int64_t lp, int m, float 
                                       const float2* sA, const float* sB, const unsigned* bm, int lane,
                                       TeamJob2<Real>* job) {
     if constexpr (sizeof(Real) == 4 && !kMixed)
-        drive_f32<kTeam>(P, lp, m, cx, cy, vo, sA, sB, bm, lane, job);
+        drive_f32<kTeam, kTeam ? kRowsBig : kRowsWarp, kTeam ? kAheadBig : true>(P, lp, m, cx, cy, vo, sA, sB, bm,
+                                                                                 lane, job);
     else
         drive_lp2<Real, kMixed, kTeam>(P, lp, m, cx, cy, vo, sA, sB, bm, lane, job);
 }

@@ -8,12 +8,11 @@
 // visited at position p.  Ties between equal sigma values go to the lowest slot, the
 // earliest constraint, box first.
 //
-// Staging: every thread computes the visit-order keys E(q) of its constraints once,
-// marks them in a bitmap of the key domain (one shared-memory atomic OR each) and
-// keeps them, two 16-bit keys per register; a prefix count of the bitmap words then
-// gives each key its rank, the constraint's visit position, and cp.async copies a_x,
-// a_y and b from HBM straight into that slot.  The LP's three segments are prefetched
-// into L2 with bulk prefetches before the keys are computed.
+// Staging: every thread computes the visit-order keys E(q) of its constraints, marks
+// them in a bitmap of the key domain (one shared-memory atomic OR each) and keeps
+// them, two 16-bit keys per register; a prefix count of the bitmap words then gives
+// each key its rank, the constraint's visit position, and cp.async copies a_x, a_y
+// and b from HBM straight into that slot.
 //
 // Iteration: the warp tests the 32 positions of an aligned window against the current
 // optimum; the first violated one (ballot) is the next step of serial Seidel, since
@@ -109,6 +108,7 @@ __device__ __forceinline__ void stage_lp2(const VisitOrder& vo, int m, const flo
     const int lane = tid & 31;
     bm[tid] = 0u;
     group_sync<T>();
+    auto key_of = [&](int q) { return vo.enc(static_cast<uint32_t>(q)); };
     const bool keep = KR > 0 && m <= KR * T;
     uint32_t kk[KR > 0 ? (KR + 1) / 2 : 1];
 #pragma unroll
@@ -116,16 +116,17 @@ __device__ __forceinline__ void stage_lp2(const VisitOrder& vo, int m, const flo
     if (keep) {
 #pragma unroll
         for (int r = 0; r < KR; ++r) {
+            if (T * r >= m) break;  // the same for every thread
             const int q = tid + T * r;
             if (q < m) {
-                const uint32_t e = vo.enc(static_cast<uint32_t>(q));
+                const uint32_t e = key_of(q);
                 atomicOr(bm + (e >> 5), 1u << (e & 31u));
                 kk[r >> 1] |= e << (16 * (r & 1));
             }
         }
     } else {
         for (int q = tid; q < m; q += T) {
-            const uint32_t e = vo.enc(static_cast<uint32_t>(q));
+            const uint32_t e = key_of(q);
             atomicOr(bm + (e >> 5), 1u << (e & 31u));
         }
     }
@@ -150,6 +151,7 @@ __device__ __forceinline__ void stage_lp2(const VisitOrder& vo, int m, const flo
     if (keep) {
 #pragma unroll
         for (int r = 0; r < KR; ++r) {
+            if (T * r >= m) break;
             const int q = tid + T * r;
             if (q < m) {
                 const uint32_t e = (kk[r >> 1] >> (16 * (r & 1))) & 0xffffu;
@@ -161,7 +163,7 @@ __device__ __forceinline__ void stage_lp2(const VisitOrder& vo, int m, const flo
         }
     } else {
         for (int q = tid; q < m; q += T) {
-            const int s = slot_of(vo.enc(static_cast<uint32_t>(q)));
+            const int s = slot_of(key_of(q));
             cp_async4(&sA[s].x, gax + q);
             cp_async4(&sA[s].y, gay + q);
             cp_async4(sB + s, gb + q);
@@ -509,10 +511,15 @@ __device__ __forceinline__ void load_window(const float2* __restrict__ sA, const
     }
 }
 
-template <bool kTeam>
+// H: the warp tests 32 H positions per step (H rows of 32, lane l holding positions
+// k + 32 h + l), which halves the serial steps of long violation-free stretches at
+// H = 2.
+template <bool kTeam, int H, bool kAhead = true>
 __device__ void drive_f32(const Params& P, int64_t lp, int m, float cx, float cy, const VisitOrder& vo,
                           const float2* __restrict__ sA, const float* __restrict__ sB, const unsigned* bm, int lane,
                           TeamJob2<float>* job) {
+    static_assert(H >= 1 && H <= 4, "one to four rows per window");
+    constexpr int kW = 32 * H;  // positions per window
     const float eps = P.eps32;
     float vx = (cx >= 0.0f) ? P.xmax : P.xmin;
     float vy = (cy >= 0.0f) ? P.ymax : P.ymin;
@@ -521,36 +528,85 @@ __device__ void drive_f32(const Params& P, int64_t lp, int m, float cx, float cy
     int d1 = (cy >= 0.0f) ? 2 : 3;
     int status = -1;
     int nviol = 0;
-    // window [k, k + 32): lane l holds position k + l in (ca, cb); `live` marks the
-    // lanes not yet known to be satisfied; (na, nb) is the next window.
+    // window [k, k + kW): row h of lane l holds position k + 32 h + l in (ca[h], cb[h]);
+    // live[h] marks the lanes of row h not yet known to be satisfied; (na, nb) is the
+    // next window.
     int k = 0;
-    unsigned live = kFull;
-    float2 ca, na;
-    float cb, nb;
-    load_window(sA, sB, lane, m, ca, cb);
-    load_window(sA, sB, 32 + lane, m, na, nb);
-    float fin = fold_finite(ca, cb, fold_finite(na, nb, 0.0f));
+    unsigned live[H];
+    float2 ca[H], na[H];
+    float cb[H], nb[H];
+    float fin = 0.0f;
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        live[h] = kFull;
+        load_window(sA, sB, 32 * h + lane, m, ca[h], cb[h]);
+        fin = fold_finite(ca[h], cb[h], fin);
+        if constexpr (kAhead) {
+            load_window(sA, sB, kW + 32 * h + lane, m, na[h], nb[h]);
+            fin = fold_finite(na[h], nb[h], fin);
+        }
+    }
     for (;;) {
-        const float s = fmaf(ca.x, vx, fmaf(ca.y, vy, -cb));
-        const float tol = fmaf(fabsf(ca.x), ex, fmaf(fabsf(ca.y), ey, eps * fabsf(cb)));
-        const unsigned bal = __ballot_sync(kFull, s > tol) & live;
-        if (bal == 0u) {
-            k += 32;
+        unsigned bal[H];
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const float s = fmaf(ca[h].x, vx, fmaf(ca[h].y, vy, -cb[h]));
+            const float tol = fmaf(fabsf(ca[h].x), ex, fmaf(fabsf(ca[h].y), ey, eps * fabsf(cb[h])));
+            bal[h] = __ballot_sync(kFull, s > tol) & live[h];
+        }
+        // the first row with a violation (hv) and its ballot (bv)
+        int hv = 0;
+        unsigned bv = bal[0];
+#pragma unroll
+        for (int h = H - 1; h >= 1; --h) {
+            if (bal[h] != 0u && bal[0] == 0u) {
+                bool earlier = false;
+#pragma unroll
+                for (int g = 1; g < h; ++g) earlier = earlier || bal[g] != 0u;
+                if (!earlier) {
+                    hv = h;
+                    bv = bal[h];
+                }
+            }
+        }
+        if (bv == 0u) {
+            k += kW;
             if (k >= m) break;
-            live = kFull;
-            ca = na;
-            cb = nb;
-            load_window(sA, sB, k + 32 + lane, m, na, nb);
-            fin = fold_finite(na, nb, fin);
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                live[h] = kFull;
+                if constexpr (kAhead) {
+                    ca[h] = na[h];
+                    cb[h] = nb[h];
+                    load_window(sA, sB, k + kW + 32 * h + lane, m, na[h], nb[h]);
+                    fin = fold_finite(na[h], nb[h], fin);
+                } else {
+                    load_window(sA, sB, k + 32 * h + lane, m, ca[h], cb[h]);
+                    fin = fold_finite(ca[h], cb[h], fin);
+                }
+            }
             continue;
         }
-        const int src = __ffs(bal) - 1;
-        live = ~((2u << src) - 1u);  // lanes above src (none when src = 31)
-        const int fslot = kBoxSlots + k + src;
+        const int src = __ffs(bv) - 1;
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            if (h < hv) live[h] = 0u;
+            else if (h == hv) live[h] = ~((2u << src) - 1u);  // lanes above src (none when src = 31)
+        }
+        const int fslot = kBoxSlots + k + 32 * hv + src;
         // ---- 1-D LP on the violated line l: lx*x + ly*y = lb
-        const float lx = __shfl_sync(kFull, ca.x, src);
-        const float ly = __shfl_sync(kFull, ca.y, src);
-        const float lb = __shfl_sync(kFull, cb, src);
+        float2 rowa = ca[0];
+        float rowb = cb[0];
+#pragma unroll
+        for (int h = 1; h < H; ++h) {
+            if (hv == h) {
+                rowa = ca[h];
+                rowb = cb[h];
+            }
+        }
+        const float lx = __shfl_sync(kFull, rowa.x, src);
+        const float ly = __shfl_sync(kFull, rowa.y, src);
+        const float lb = __shfl_sync(kFull, rowb, src);
         const float nrm2 = lx * lx + ly * ly;
         if (!(nrm2 != 0.0f)) {  // 0.x <= lb < 0 (NaN data also stops here)
             status = kInfeasible;
@@ -625,7 +681,8 @@ __device__ void drive_f32(const Params& P, int64_t lp, int m, float cx, float cy
     }
     // positions never loaded (the LP stopped early) still take part in the finiteness check
     if (P.check_finite) {
-        for (int p = k + 64 + lane; p < m; p += 32) fin = fold_finite(sA[kBoxSlots + p], sB[kBoxSlots + p], fin);
+        for (int p = k + (kAhead ? 2 : 1) * kW + lane; p < m; p += 32)
+            fin = fold_finite(sA[kBoxSlots + p], sB[kBoxSlots + p], fin);
     }
     const bool bad_data = P.check_finite && __any_sync(kFull, fin != fin);
     const bool bad_obj = !(fabsf(cx) <= 3.402823466e38f) || !(fabsf(cy) <= 3.402823466e38f);
