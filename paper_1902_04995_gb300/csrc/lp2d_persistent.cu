@@ -10,7 +10,7 @@
 //            are read from global memory in visit order instead);
 //   phase 2: LPs with more than kCapSmall and at most kCapMid constraints, one per
 //            warp for warps 0 and 1, each with half of the stage (their 1-D LPs are
-//            too short for the helpers, so two drivers share a CTA's stage);
+//            too short for helpers, so two drivers share a CTA's stage);
 //   phase 3: LPs with at most kCapSmall constraints, one per warp, each warp with a
 //            quarter of the stage.
 // Large LPs therefore start first and small ones fill the tail.  The last CTA to
@@ -28,26 +28,25 @@ constexpr int kMidSlots = kStageSlots / kMidWarps;          // their stage slots
 static_assert(kWarpSlots - kBoxSlots >= kCapSmall, "quarter-stage capacity");
 static_assert(kMidSlots - kBoxSlots >= kCapMid && kCapMid <= 1024, "half-stage capacity (32-word key bitmap)");
 static_assert(kStageSlots - kBoxSlots >= kCapBig && kCapBig <= 4096, "stage capacity (128-word key bitmap)");
-// Keys a thread keeps in registers between the staging passes (two per register):
-// quarter-stage and CTA-staged LPs keep them; a half-stage LP computes them again
-// (fewer registers and less code).
+// Keys a thread keeps in registers between the staging passes (two per register).
 constexpr int kKeysSmall = (kCapSmall + 31) / 32;
-constexpr int kKeysMid = 0;
+constexpr int kKeysMid = 0;  // computed again: fewer registers and less code
 constexpr int kKeysBig = (kCapBig + 127) / 128;
 
-// Rows of 32 positions the FP32 driver tests per step: large LPs, warp LPs.
+// Rows of 32 positions the FP32 driver tests per step, per phase: more rows shorten the
+// serial chain of an LP, fewer cost fewer instructions.
 constexpr int kRowsBig = 2;
-constexpr int kRowsWarp = 1;
-constexpr bool kAheadBig = true;  // large LPs: load the next window one step ahead
+constexpr int kRowsMid = 1;
+constexpr int kRowsSmall = 1;
 
-// The FP32 iterations have their own driver; the other precisions share drive_lp2.
-template <typename Real, bool kMixed, bool kTeam>
+// The FP32 iterations have their own driver (Rows rows of 32 positions per step); the
+// other precisions share drive_lp2.
+template <typename Real, bool kMixed, bool kTeam, int Rows>
 __device__ __forceinline__ void drive(const Params& P, int64_t lp, int m, float cx, float cy, const VisitOrder& vo,
                                       const float2* sA, const float* sB, const unsigned* bm, int lane,
                                       TeamJob2<Real>* job) {
     if constexpr (sizeof(Real) == 4 && !kMixed)
-        drive_f32<kTeam, kTeam ? kRowsBig : kRowsWarp, kTeam ? kAheadBig : true>(P, lp, m, cx, cy, vo, sA, sB, bm,
-                                                                                 lane, job);
+        drive_f32<kTeam, Rows>(P, lp, m, cx, cy, vo, sA, sB, bm, lane, job);
     else
         drive_lp2<Real, kMixed, kTeam>(P, lp, m, cx, cy, vo, sA, sB, bm, lane, job);
 }
@@ -158,11 +157,11 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
             }
             VisitOrder vo;
             warp_visit_order(vo, P.seed + static_cast<uint64_t>(lp), static_cast<uint32_t>(m), lane);
-            stage_lp2<128, kKeysBig>(vo, m, P.ax + base, P.ay + base, P.b + base, sA, sB, s_bm, s_pre, s_wsum, tid);
+            stage_lp2<128, 128, kKeysBig>(vo, m, P.ax + base, P.ay + base, P.b + base, sA, sB, s_bm, s_pre, s_wsum, tid);
             cp_async_wait_all();
             __syncthreads();
             if (warp == 0)
-                drive<Real, kMixed, true>(P, lp, m, s_obj[2 * i], s_obj[2 * i + 1], vo, sA, sB, s_bm, lane, &job);
+                drive<Real, kMixed, true, kRowsBig>(P, lp, m, s_obj[2 * i], s_obj[2 * i + 1], vo, sA, sB, s_bm, lane, &job);
             else
                 team_helper2<Real, kMixed>(sA, sB, &job, tid);
             __syncthreads();
@@ -195,10 +194,11 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
                 const float cx = __shfl_sync(kFull, cx_l, i), cy = __shfl_sync(kFull, cy_l, i);
                 VisitOrder vo;
                 warp_visit_order(vo, P.seed + static_cast<uint64_t>(lp), static_cast<uint32_t>(m), lane);
-                stage_lp2<32, kKeysMid>(vo, m, P.ax + base, P.ay + base, P.b + base, hA, hB, hbm, hpre, nullptr, lane);
+                stage_lp2<32, 32, kKeysMid>(vo, m, P.ax + base, P.ay + base, P.b + base, hA, hB, hbm, hpre, nullptr,
+                                            lane);
                 cp_async_wait_all();
                 __syncwarp();
-                drive<Real, kMixed, false>(P, lp, m, cx, cy, vo, hA, hB, hbm, lane, nullptr);
+                drive<Real, kMixed, false, kRowsMid>(P, lp, m, cx, cy, vo, hA, hB, hbm, lane, nullptr);
                 __syncwarp();  // all lanes are done with the stage before it is overwritten
             }
         }
@@ -235,10 +235,10 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
             const float cx = __shfl_sync(kFull, cx_l, i), cy = __shfl_sync(kFull, cy_l, i);
             VisitOrder vo;
             warp_visit_order(vo, P.seed + static_cast<uint64_t>(lp), static_cast<uint32_t>(m), lane);
-            stage_lp2<32, kKeysSmall>(vo, m, P.ax + base, P.ay + base, P.b + base, wA, wB, wbm, wpre, nullptr, lane);
+            stage_lp2<32, 32, kKeysSmall>(vo, m, P.ax + base, P.ay + base, P.b + base, wA, wB, wbm, wpre, nullptr, lane);
             cp_async_wait_all();
             __syncwarp();
-            drive<Real, kMixed, false>(P, lp, m, cx, cy, vo, wA, wB, wbm, lane, nullptr);
+            drive<Real, kMixed, false, kRowsSmall>(P, lp, m, cx, cy, vo, wA, wB, wbm, lane, nullptr);
             __syncwarp();  // all lanes are done with the stage before it is overwritten
         }
     }

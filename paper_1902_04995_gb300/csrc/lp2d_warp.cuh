@@ -76,9 +76,18 @@ __device__ __forceinline__ float fold_finite(float2 a, float b, float acc) {
     return fmaf(a.x, 0.0f, fmaf(a.y, 0.0f, fmaf(b, 0.0f, acc)));
 }
 
+// Barrier of a staging group: a warp, a pair of warps (named barrier `bar`), or the CTA.
+// The pair barrier's id (3 or 4) is selected among immediates, so that the kernel
+// declares only the barriers it uses.
+__device__ __forceinline__ void pair_barrier(int bar) {
+    if (bar == 3) asm volatile("bar.sync 3, 64;\n" ::: "memory");
+    else asm volatile("bar.sync 4, 64;\n" ::: "memory");
+}
+
 template <int T>
-__device__ __forceinline__ void group_sync() {
+__device__ __forceinline__ void group_sync(int bar) {
     if constexpr (T == 32) __syncwarp();
+    else if constexpr (T == 64) pair_barrier(bar);
     else __syncthreads();
 }
 
@@ -93,21 +102,23 @@ __device__ __forceinline__ void write_box2(const Params& P, float2* sA, float* s
 }
 
 // ------------------------------------------------------------------ staging
-// T threads (one warp, or the CTA's 128) stage the m constraints at gax/gay/gb into
-// slots 4.. of sA/sB in visit order.  The key domain must fit T bitmap words
-// (m <= 1024 for a warp, m <= 4096 for 128 threads).  bm, pre: T words each (bm keeps
-// the LP's key bitmap afterwards); wsum: T/32 words.  Thread tid stages constraints
-// tid, tid + T, ...; when there are at most KR of them per thread their keys are kept
-// in registers between the two passes, otherwise they are computed again.
-// Completion: cp_async_wait_all() then group_sync<T>().
-template <int T, int KR>
+// T threads (one warp, a pair of warps, or the CTA's 128) stage the m constraints at
+// gax/gay/gb into slots 4.. of sA/sB in visit order.  The key domain must fit NW
+// bitmap words (NW = 32: m <= 1024; NW = 128: m <= 4096); threads 0..NW-1 own one
+// word each.  bm, pre: NW words each (bm keeps the LP's key bitmap afterwards); wsum:
+// NW/32 words.  Thread tid stages constraints tid, tid + T, ...; when there are at
+// most KR of them per thread their keys are kept in registers between the two
+// passes, otherwise they are computed again.  bar: the pair's named barrier (T = 64).
+// Completion: cp_async_wait_all() then group_sync<T>(bar).
+template <int T, int NW, int KR>
 __device__ __forceinline__ void stage_lp2(const VisitOrder& vo, int m, const float* __restrict__ gax,
                                           const float* __restrict__ gay, const float* __restrict__ gb,
-                                          float2* sA, float* sB, unsigned* bm, int* pre, int* wsum, int tid) {
-    static_assert(T == 32 || T == 128, "one warp or four");
+                                          float2* sA, float* sB, unsigned* bm, int* pre, int* wsum, int tid,
+                                          int bar = 0) {
+    static_assert((T == 32 && NW == 32) || (T == 64 && NW == 32) || (T == 128 && NW == 128), "staging group");
     const int lane = tid & 31;
-    bm[tid] = 0u;
-    group_sync<T>();
+    if (tid < NW) bm[tid] = 0u;
+    group_sync<T>(bar);
     auto key_of = [&](int q) { return vo.enc(static_cast<uint32_t>(q)); };
     const bool keep = KR > 0 && m <= KR * T;
     uint32_t kk[KR > 0 ? (KR + 1) / 2 : 1];
@@ -130,19 +141,21 @@ __device__ __forceinline__ void stage_lp2(const VisitOrder& vo, int m, const flo
             atomicOr(bm + (e >> 5), 1u << (e & 31u));
         }
     }
-    group_sync<T>();
-    const unsigned w = bm[tid];
-    const int c = __popc(w);
-    int incl = warp_inclusive_scan(c, lane);
-    if constexpr (T > 32) {
-        if (lane == 31) wsum[tid >> 5] = incl;
-        __syncthreads();
-        int base = 0;
-        for (int i = 0; i < (tid >> 5); ++i) base += wsum[i];
-        incl += base;
+    group_sync<T>(bar);
+    if (tid < NW) {  // whole warps
+        const unsigned w = bm[tid];
+        const int c = __popc(w);
+        int incl = warp_inclusive_scan(c, lane);
+        if constexpr (NW > 32) {
+            if (lane == 31) wsum[tid >> 5] = incl;
+            __syncthreads();
+            int base = 0;
+            for (int i = 0; i < (tid >> 5); ++i) base += wsum[i];
+            incl += base;
+        }
+        pre[tid] = incl - c;
     }
-    pre[tid] = incl - c;
-    group_sync<T>();
+    group_sync<T>(bar);
     // slot of key e: 4 + (number of smaller keys)
     auto slot_of = [&](uint32_t e) {
         const int wi = static_cast<int>(e >> 5);
@@ -201,8 +214,16 @@ __device__ __forceinline__ void wu_range2(const float2* __restrict__ sA, const f
     for (int j = j0; j < jend; j += STRIDE) {
         const float2 g = sA[j];
         const Real gx = g.x, gy = g.y, gb = sB[j];
-        Real den = (gx * ux + gy * uy) + Real(0);
-        const Real num = gb - (gx * p0x + gy * p0y);
+        Real den, num;
+        if constexpr (sizeof(Real) == 4 && !kFlag && !kMixed) {
+            // fused forms: the inner fma's +0 addend keeps den off -0 (an exact zero
+            // sum rounds to +0), as the + 0 below does
+            den = fmaf(gx, ux, fmaf(gy, uy, 0.0f));
+            num = fmaf(-gx, p0x, fmaf(-gy, p0y, gb));
+        } else {
+            den = (gx * ux + gy * uy) + Real(0);
+            num = gb - (gx * p0x + gy * p0y);
+        }
         Real t = real_div<Real>(num, den);
         if constexpr (kFlag || kMixed) {
             const bool is_near = den * den < ml.lim * (gx * gx + gy * gy);
@@ -649,19 +670,19 @@ __device__ void drive_f32(const Params& P, int64_t lp, int m, float cx, float cy
             }
         } else {
             if (fslot <= 32) {
-                // a short 1-D LP: one slot per lane, no loop
-                if (lane < fslot) {
-                    const float2 g = sA[lane];
-                    const float gb = sB[lane];
-                    const float den = (g.x * ux + g.y * uy) + 0.0f;
-                    const float t = __fdividef(gb - (g.x * p0x + g.y * p0y), den);
-                    const bool right = den >= 0.0f;
-                    if (right && t < thi) {  // t is NaN for 0 / 0: no bound
-                        thi = t;
-                        phi = lane;
-                    }
-                    tlo = right ? tlo : t;
+                // a short 1-D LP: one slot per lane, no loop; lanes at or past fslot
+                // load a later slot of the stage and ignore it
+                const float2 g = sA[lane];
+                const float gb = sB[lane];
+                const float den = fmaf(g.x, ux, fmaf(g.y, uy, 0.0f));
+                const float t = __fdividef(fmaf(-g.x, p0x, fmaf(-g.y, p0y, gb)), den);
+                const bool in = lane < fslot;
+                const bool right = den >= 0.0f;
+                if (in && right && t < thi) {  // t is NaN for 0 / 0: no bound
+                    thi = t;
+                    phi = lane;
                 }
+                tlo = (in && !right) ? t : tlo;
             } else {
                 wu_range2<float, 32>(sA, sB, lane, fslot, p0x, p0y, ux, uy, thi, phi, tlo);
             }
