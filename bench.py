@@ -183,6 +183,58 @@ def oracle_rate(batch, max_seconds: float, min_reps: int = 1, threads: int | Non
     return done / el, threads, done, el
 
 
+def precision_table(dev, seed):
+    """Part of the CPU-baseline leg: the error of each precision mode against the FP64
+    oracle (run here on the host cores) on the collision-avoidance workload and on the
+    near-parallel-pairs workload, with the GPU time of one solve per mode."""
+    import torch
+
+    import oracle
+    from paper_1902_04995_gb300 import lp2d, workloads
+
+    oracle.build()
+    rows = []
+    for name, batch in (("collision_16384", workloads.collision(seed=seed)),
+                        ("near_parallel_4096", workloads.near_parallel_pairs(4096, seed=seed))):
+        t0 = time.perf_counter()
+        ref = oracle.solve_batch(batch["ax"], batch["ay"], batch["b"], batch["offsets"], batch["obj"], batch["box"],
+                                 seed=seed, threads=os.cpu_count() or 1)
+        oracle_s = time.perf_counter() - t0
+        t = {k: torch.from_numpy(np.ascontiguousarray(batch[k])).to(dev) for k in ("ax", "ay", "b", "offsets", "obj")}
+        n_lp = len(batch["offsets"]) - 1
+        c = batch["obj"].astype(np.float64)
+        owner = np.repeat(np.arange(n_lp), np.diff(batch["offsets"]))
+        for mode, prec in (("fp32", lp2d.PREC_FP32), ("fp32_f64isect", lp2d.PREC_FP32_F64ISECT),
+                           ("fp64", lp2d.PREC_FP64)):
+            solver = lp2d.Solver(n_lp, lp2d.default_options(seed=seed, precision=prec), device=dev)
+            solver(t["ax"], t["ay"], t["b"], t["offsets"], t["obj"].reshape(-1), batch["box"])
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(10):
+                solver(t["ax"], t["ay"], t["b"], t["offsets"], t["obj"].reshape(-1), batch["box"])
+            e1.record()
+            torch.cuda.synchronize()
+            xy = solver.out_xy.cpu().numpy().reshape(-1, 2).astype(np.float64)
+            st = solver.out_status.cpu().numpy()
+            both = (st != oracle.INFEASIBLE) & (ref["status"] != oracle.INFEASIBLE) & (st != oracle.BAD_INPUT)
+            f = np.einsum("ij,ij->i", xy, c)
+            fr = np.einsum("ij,ij->i", ref["xy"], c)
+            rel = np.abs(f - fr)[both] / np.maximum(np.abs(fr[both]), 1.0)
+            # largest violation of any constraint by the returned point, relative to max(1, |x|)
+            slack = batch["ax"] * xy[owner, 0] + batch["ay"] * xy[owner, 1] - batch["b"]
+            scale = np.maximum(1.0, np.abs(xy[owner]).max(axis=1))
+            viol = np.where(both[owner], slack / scale, -np.inf)
+            rows.append({"workload": name, "mode": mode, "n_lp": n_lp, "ms_per_solve": e0.elapsed_time(e1) / 10,
+                         "status_mismatches": int((st != ref["status"]).sum()),
+                         "max_rel_objective_error": float(rel.max(initial=0.0)),
+                         "p99_rel_objective_error": float(np.percentile(rel, 99)) if rel.size else 0.0,
+                         "max_rel_constraint_violation": float(max(viol.max(initial=-np.inf), 0.0)),
+                         "oracle_seconds": oracle_s})
+            del solver
+    return rows
+
+
 def sample_batch(batch, n_lp_sample):
     """The first n_lp_sample LPs of a batch (the CPU baselines' bounded sample)."""
     off = batch["offsets"][: n_lp_sample + 1]
@@ -680,6 +732,11 @@ def run_ours(args):
                "sample": f"first 32768 LPs of the {WORKLOAD} workload ({int(sample['offsets'][-1])} constraints), "
                          f"repeated: {done} LPs in {el:.1f} s on {threads} threads"}
 
+    # the per-mode error table against the oracle (part of the CPU-baseline leg)
+    precision = None
+    if not args.no_cpu_baseline and world == 1:
+        precision = precision_table(dev, args.seed)
+
     peak, peak_kind = measured_peaks()
     achieved = algo_bytes / (ms * 1e-3) / 1e9
     clocks = sampler.summary(t_on, t_off, t_wide0)
@@ -705,6 +762,7 @@ def run_ours(args):
                 "status_equal_device_resident": e2e_status_equal,
                 "serial_ms_per_step": ms_e2e_serial},
         "cpu_baseline": cpu,
+        "precision": precision,
         "serve": serve_line,
         "lp3d": lp3d_line,
         "lpnd": lpnd_lines,

@@ -212,6 +212,39 @@ def collision_batch(n_lp, seed=DEFAULT_SEED, near_parallel_frac=0.05, box=DEFAUL
 
 
 # ----------------------------------------------------------------- named workloads
+def near_parallel_pairs(n_lp=4096, seed=DEFAULT_SEED, delta=1e-5, margin=1e-3, half=1000.0, tilt=-0.5):
+    """LPs whose outcome is the intersection of two nearly parallel lines.
+
+    LP l holds n1 . x <= 0 and n2 . x >= w (stored as -n2 . x <= -w), where n1 has a
+    uniform angle and n2 is n1 turned by an angle of delta * U[0.5, 2].  The lines
+    cross on the line n1 . x = 0 at s* = w / det(n1, n2) along u = (-n1_y, n1_x); w
+    puts that crossing a fraction `margin` inside (even l) or outside (odd l) the box
+    of half-width `half`, so the LP is feasible with its optimum at the crossing, or
+    infeasible.  The objective n1 + tilt * u makes both visit orders end in the 1-D LP
+    on one of the two lines with the other as its bound, where the crossing is the
+    quotient of two quantities about delta small: FP32 resolves it only to about
+    2^-24 / delta relative, FP64 to about 2^-53 / delta.  Every quantity is computed
+    from the float32 values actually stored."""
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0.0, 2.0 * np.pi, n_lp)
+    d = delta * rng.uniform(0.5, 2.0, n_lp)
+    n1 = np.stack([np.cos(a), np.sin(a)], 1).astype(np.float32)
+    n2 = np.stack([np.cos(a + d), np.sin(a + d)], 1).astype(np.float32)
+    n1d, n2d = n1.astype(np.float64), n2.astype(np.float64)
+    det = n1d[:, 0] * n2d[:, 1] - n1d[:, 1] * n2d[:, 0]
+    u = np.stack([-n1d[:, 1], n1d[:, 0]], 1)
+    f = np.where(np.arange(n_lp) % 2 == 0, 1.0 - margin, 1.0 + margin)
+    w = (f * half * det / np.abs(u).max(1)).astype(np.float32)
+    cons = np.zeros((n_lp, 2, 3), np.float32)
+    cons[:, 0, :2] = n1
+    cons[:, 1, :2] = -n2
+    cons[:, 1, 2] = -w
+    cons = cons.reshape(-1, 3)
+    return {"ax": cons[:, 0].copy(), "ay": cons[:, 1].copy(), "b": cons[:, 2].copy(),
+            "offsets": np.arange(0, 2 * n_lp + 1, 2, dtype=np.int64),
+            "obj": (n1d + tilt * u).astype(np.float32), "box": (-half, half, -half, half)}
+
+
 def plain_small(seed=DEFAULT_SEED):
     """256 LPs x 64 constraints, all feasible."""
     return disk_batch(np.full(256, 64, dtype=np.int64), seed=seed)

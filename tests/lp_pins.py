@@ -127,3 +127,4 @@ def least_violation_batch(batch, tmax_factor=8.0):
     obj = np.tile(np.array([0.0, 0.0, -1.0], np.float32), (n_lp, 1))
     return {"ax": ax, "ay": ay, "az": az, "b": np.asarray(batch["b"], np.float32), "offsets": batch["offsets"],
             "obj": obj, "box": box + (0.0, tmax)}
+

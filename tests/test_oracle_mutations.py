@@ -29,6 +29,7 @@ DETECT_2D = [
     lambda: pins2.test_regular_ngon_closed_form(oracle, 8),
     lambda: [pins2.test_hand_solved_golden(oracle, case) for case in lp_pins.load_hand_lps()],
     lambda: pins2.test_antiparallel_pair_infeasible_and_strip(oracle),
+    lambda: pins2.test_duplicate_pair_reports_the_earlier_visited_copy(oracle),
 ]
 DETECT_3D = [pins3.test_brute_force_on_tiny_lps, pins3.test_cube_and_box_closed_forms,
              pins3.test_octahedron_closed_form]
@@ -49,6 +50,12 @@ MUTATIONS = [
     ("2d_wrong_start_corner", "seidel_oracle.c", "double x0 = (cx >= 0.0) ? box[1] : box[0];",
      "double x0 = (cx >= 0.0) ? box[0] : box[1];", DETECT_2D),
     ("2d_line_direction", "seidel_oracle.c", "double ux = -hy, uy = hx;", "double ux = hy, uy = hx;", DETECT_2D),
+    ("2d_endpoint_reading_r2", "seidel_oracle.c", "if (cu > 0.0) { t = u_right; e = id_right; }",
+     "if (cu >= 0.0) { t = u_right; e = id_right; }", DETECT_2D),
+    ("2d_tie_reading_r3_left", "seidel_oracle.c", "if (t > u_left) { u_left = t; id_left = gid; }",
+     "if (t >= u_left) { u_left = t; id_left = gid; }", DETECT_2D),
+    ("2d_tie_reading_r3_right", "seidel_oracle.c", "if (t < u_right) { u_right = t; id_right = gid; }",
+     "if (t <= u_right) { u_right = t; id_right = gid; }", DETECT_2D),
     ("2d_parallel_rule", "seidel_oracle.c", "} else if (num < 0.0) {  /* parallel and excluding the line */",
      "} else if (num > 0.0) {  /* parallel and excluding the line */", DETECT_2D),
     ("3d_objective_end", "seidel3_oracle.c", "if (cd > 0.0) { tau = hi; e = id_hi; }",

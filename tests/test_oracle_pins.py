@@ -103,7 +103,8 @@ def test_perm_position_rank_uncorrelated(oracle_mod):
 # ------------------------------------------------------------- hand-solved LPs
 @pytest.mark.parametrize("case", lp_pins.load_hand_lps(), ids=lambda c: c["name"])
 def test_hand_solved_golden(oracle_mod, case):
-    for seed in (0, 1, 7):
+    # seeds 0 and 2 visit the two constraints of a two-constraint LP in both orders
+    for seed in (0, 1, 2, 7):
         st, xy, _, _ = solve_one(oracle_mod, case["cons"], case["obj"], case["box"], seed)
         assert st == case["status"]
         if case["xyf"] is not None:
@@ -301,3 +302,57 @@ def test_against_scipy_highs(oracle_mod):
         else:
             assert res.status == 0
             assert -res.fun == pytest.approx(c @ r["xy"][lp], rel=1e-7, abs=1e-7)
+
+
+# ------------------------------------------------------ reading R3 (ties)
+def duplicate_defining_constraint_batch(oracle, n_lp, seed):
+    """LPs of the disk family, each with an exact copy of one constraint through its
+    optimum appended: the constraint the oracle reports as the bound of the last 1-D
+    LP (seed `seed`).  Returns the batch and, per LP, the indices (original, copy) of
+    the duplicated pair.  Whenever the pair's line bounds a later 1-D LP, the two give
+    equal sigma values, so the pair tests the tie rule (earliest position first)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(20), np.log(300), n_lp)).astype(np.int64)
+    base = workloads.disk_batch(sizes, seed=seed, infeasible_frac=0.0)
+    ref = oracle.solve_batch(base["ax"], base["ay"], base["b"], base["offsets"], base["obj"], base["box"],
+                             seed=seed, want_def=True)
+    cols = {k: [] for k in ("ax", "ay", "b")}
+    pair, sz = [], []
+    for l in range(n_lp):
+        s, e = int(base["offsets"][l]), int(base["offsets"][l + 1])
+        d = int(ref["def"][l][1])
+        if ref["status"][l] != oracle.OPTIMAL or d < 0:
+            d = 0  # any constraint: the LP then rarely exercises the rule
+        for k in cols:
+            v = base[k][s:e]
+            cols[k].append(np.r_[v, v[d:d + 1]])
+        pair.append((d, e - s))
+        sz.append(e - s + 1)
+    off = np.zeros(n_lp + 1, np.int64)
+    np.cumsum(sz, out=off[1:])
+    batch = {k: np.concatenate(v).astype(np.float32) for k, v in cols.items()}
+    batch.update({"offsets": off, "obj": base["obj"], "box": base["box"]})
+    return batch, np.asarray(pair, np.int64)
+
+def test_duplicate_pair_reports_the_earlier_visited_copy(oracle_mod):
+    # An exact copy of a constraint through the optimum: both copies give the same
+    # sigma in every 1-D LP that they bound, and a later copy is never violated (the
+    # optimum satisfies its twin).  So whichever of the two the oracle reports must be
+    # the one visited first (reading R3), whatever the visit order.
+    batch, pair = duplicate_defining_constraint_batch(oracle_mod, 600, seed=31)
+    seed = 5
+    ref = oracle_mod.solve_batch(batch["ax"], batch["ay"], batch["b"], batch["offsets"], batch["obj"], batch["box"],
+                                 seed=seed, want_def=True)
+    exercised = 0
+    for l in range(len(pair)):
+        d = ref["def"][l][:2]
+        a, b = pair[l]
+        hit = [x for x in d if x in (a, b)]
+        if ref["status"][l] == oracle_mod.INFEASIBLE or not hit:
+            continue
+        m = int(batch["offsets"][l + 1] - batch["offsets"][l])
+        pos = np.argsort(oracle_mod.perm_array(seed + l, m))  # visit position of each constraint
+        assert len(hit) == 1
+        assert pos[hit[0]] == min(pos[a], pos[b]), (l, d, a, b)
+        exercised += 1
+    assert exercised >= 400
