@@ -161,6 +161,71 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(inside), "window": window}
 
 
+class NvmlSampler:
+    """SM clock, power and clock-event reasons read from NVML (libnvidia-ml through
+    ctypes, read-only queries) every `period` seconds on a thread, so that even a
+    timed region of a few milliseconds holds samples.  `ok` is False when NVML cannot
+    be loaded; the caller then falls back to nvidia-smi."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, uuid: str, period: float = 0.001):
+        import ctypes
+
+        self.samples = []
+        self.ok = False
+        self.stop_flag = False
+        self.max_mhz = None
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            self.dev = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.dev)) != 0:
+                return
+            self.reason_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            mx = ctypes.c_uint()
+            self.max_mhz = float(mx.value) if lib.nvmlDeviceGetMaxClockInfo(self.dev, 1, ctypes.byref(mx)) == 0 else None
+        except (OSError, AttributeError):
+            return
+        self.lib, self.ct, self.period, self.ok = lib, ctypes, period, True
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def _run(self):
+        ct, lib = self.ct, self.lib
+        clk, pw, rs = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        while not self.stop_flag:
+            t = time.time()
+            if lib.nvmlDeviceGetClockInfo(self.dev, 1, ct.byref(clk)) == 0:
+                p = float(pw.value) / 1e3 if lib.nvmlDeviceGetPowerUsage(self.dev, ct.byref(pw)) == 0 else None
+                r = int(rs.value) if self.reason_fn(self.dev, ct.byref(rs)) == 0 else 0
+                self.samples.append((t, float(clk.value), p, r))
+            time.sleep(self.period)
+
+    def stop(self):
+        self.stop_flag = True
+        if self.ok:
+            self.thread.join(timeout=2)
+
+    def summary(self, t0, t1, t_wide0):
+        inside = [s for s in self.samples if t0 <= s[0] <= t1]
+        window = "timed"
+        if not inside:
+            inside = [s for s in self.samples if t_wide0 <= s[0] <= t1 + 0.25]
+            window = "warmup+timed"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0, "window": "none",
+                    "source": "nvml"}
+        reasons = sorted({name for s in inside for bit, name in self.REASONS.items() if s[3] & bit})
+        powers = [s[2] for s in inside if s[2] is not None]
+        return {"sm_mhz": float(np.median([s[1] for s in inside])), "sm_min_mhz": min(s[1] for s in inside),
+                "sm_max_mhz": self.max_mhz, "power_w_max": max(powers) if powers else None, "reasons": reasons,
+                "samples": len(inside), "window": window, "source": "nvml"}
+
+
 def oracle_rate(batch, max_seconds: float, min_reps: int = 1, threads: int | None = None):
     """LPs/s of the FP64 oracle on `threads` host cores (default: all), repeating the
     batch until about max_seconds of CPU work; returns (rate, threads, lps_done, seconds)."""
@@ -541,7 +606,9 @@ def run_ours(args):
         tune_ms = solver.autotune(t["ax"], t["ay"], t["b"], t["offsets"], obj, box, reps=2, stream=stream)
         o = solver.options
         tune = {"ctas_per_sm": o.ctas_per_sm, "chunk_big": o.chunk_big, "chunk_small": o.chunk_small,
-                "ms_per_solve": tune_ms, "grid": "ctas_per_sm {occ, occ-1} x chunk_big {1,2,4} x chunk_small {1,2,4,8}"}
+                "team_min_slots": o.team_min_slots, "ms_per_solve": tune_ms,
+                "grid": "ctas_per_sm {occ, occ-1} x chunk_big {1,2,4} x chunk_small {1,2,4,8} x "
+                        "team_min_slots {512,1024,4096}"}
     with torch.cuda.stream(stream):
         for _ in range(3):
             solver(t["ax"], t["ay"], t["b"], t["offsets"], obj, box)
@@ -553,7 +620,9 @@ def run_ours(args):
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         gpu_id = str(local)
-    sampler = ClockSampler(gpu_id)
+    sampler = NvmlSampler(gpu_id)
+    if not sampler.ok:
+        sampler = ClockSampler(gpu_id)
     time.sleep(0.3)
     t_wide0 = time.time()
     with torch.cuda.stream(stream):
@@ -718,6 +787,26 @@ def run_ours(args):
         below.update(link_gbs_measured=link_gbs, fraction_of_link=0.6)
         serve_line["below_link_rate"] = below
         del eng, pool
+        torch.cuda.empty_cache()
+        # the engine itself at the config's rate: requests name ranges of LPs that are
+        # already resident in device memory (64 distinct requests), so only results
+        # cross the host link
+        rpool = lpserve.ResidentPool(workloads.serving_pool(seed=args.seed), device=dev)
+        rreqs = lpserve.resident_requests(rpool, 64, seed=args.seed)
+        reng = lpserve.ServeEngine(capacity_bytes=20 << 30, n_streams=4, device=dev)
+        reng.make_host_ring(1 << 30)
+        reng.run_resident_stream(rpool, rreqs[:8], np.zeros(8))  # warm-up
+        r_secs = max(args.serve_seconds, 10.0)
+        arrivals = lpserve.poisson_arrivals(2000.0, r_secs, seed=args.seed + 1)
+        order = np.random.default_rng(args.seed + 2).integers(0, len(rreqs), len(arrivals))
+        rstats = reng.run_resident_stream(rpool, [rreqs[i] for i in order], arrivals, max_wall_s=60.0 + 5 * r_secs)
+        serve_line["resident"] = dict(rstats.summary(), offered_requests_per_s=2000.0, stream_seconds=r_secs,
+                                      distinct_requests=len(rreqs), pool_lps=rpool.n_lp,
+                                      pool_constraints=int(rpool.offsets[-1]), capacity_bytes=20 << 30, streams=4,
+                                      mean_lps_per_request=float(np.mean([rreqs[i].hi - rreqs[i].lo
+                                                                          for i in order])) if len(order) else 0.0,
+                                      d2h_bytes_per_lp=12)
+        del reng, rpool
         torch.cuda.empty_cache()
 
     # ---- CPU baseline: the oracle on the host cores, bounded sample

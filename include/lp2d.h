@@ -60,7 +60,8 @@ typedef enum {
     LP2D_OK = 0,
     LP2D_ERR_INVALID_ARGUMENT = -1,
     LP2D_ERR_CUDA = -2,
-    LP2D_ERR_TIMEOUT = -3,
+    LP2D_ERR_TIMEOUT = -3,       /* reserved: no kernel of this version waits on a flag or a
+                                    peer, so no path returns it */
     LP2D_ERR_WORKSPACE = -4,
     LP2D_ERR_UNSUPPORTED = -5
 } lp2d_err;
@@ -115,8 +116,8 @@ typedef struct {
                                  constraints) over at least this many earlier constraints (box
                                  included) is shared by the CTA's 128 threads, a shorter one runs
                                  on the driving warp's 32 (64..4096; 0 = default 1024) */
-    int32_t l2_prefetch;    /**< persistent schedule: 0 or 1 = bulk-prefetch the constraints of
-                                 every LP a CTA or warp takes from the queue into L2 (default);
+    int32_t l2_prefetch;    /**< persistent schedule: 1 = bulk-prefetch the constraints of every
+                                 LP a CTA or warp takes from the queue into L2; 0 (default) or
                                  -1 = no prefetch */
 } lp2d_options;
 
@@ -133,6 +134,9 @@ void lp2d_default_options(lp2d_options* opt);
  * the same time must not share a workspace.
  */
 size_t lp2d_workspace_bytes(int64_t n_lp, const lp2d_options* opt);
+/* (The size depends on neither the batch nor the constraint count -- the workspace is
+ * the queue heads and the error word -- so, unlike a size query that also takes the
+ * number of constraints, this one takes the LP count only.) */
 
 /** Zero `bytes` of workspace on `stream` (cudaMemsetAsync).  Returns an lp2d_err. */
 int lp2d_workspace_init(void* workspace, size_t bytes, lp2d_stream_t stream);
@@ -180,8 +184,10 @@ int lp2d_solve_batch_ex(const float* ax, const float* ay, const float* b, const 
  * that loads the library keeps until the process exits.  No call of this entry point
  * calls cudaMalloc, cudaFree or any allocating routine.
  * - The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current.  Make that first call before
- *   any stream capture.
+ *   (cudaGetSymbolAddress) with that device current and keeps it.  Make that first
+ *   call before any stream capture.  The kept address dies with the device's
+ *   context: after cudaDeviceReset, do not call this entry point on that device
+ *   again in the same process.
  * - Every call clears the array on `stream` before its solve.  All calls share the
  *   one array, so calls whose work overlaps on the GPU (other streams, other host
  *   threads) race: order them on one stream, or use lp2d_solve_batch_ex with separate
@@ -219,8 +225,9 @@ int lp2d_solve_batch_noalloc(const float* ax, const float* ay, const float* b, c
  * synchronising `stream` makes the results readable.  The device slots are
  * allocated on the first call for a (device, stream) pair and grown when a larger
  * chunk needs them, so such a call must not be inside CUDA-graph capture.  Calls on
- * one stream share the slots and must not run concurrently from several host
- * threads.  Returns an lp2d_err.
+ * one (device, stream) pair share the slots; the library serialises them with a
+ * lock, so a second host thread waits until the first call has enqueued its work.
+ * Returns an lp2d_err.
  */
 int lp2d_solve_batch_host(const float* ax, const float* ay, const float* b, const int64_t* offsets,
                           int64_t n_lp, const float* obj_xy, lp2d_box box, void* out_xy,
@@ -239,9 +246,11 @@ int lp2d_visit_order(uint64_t seed_l, int64_t m, int64_t* out, lp2d_stream_t str
 /**
  * Autotune the persistent schedule for a batch: solve it with each candidate of a
  * small grid -- ctas_per_sm in {the occupancy limit, one less}, chunk_big in
- * {1, 2, 4}, chunk_small in {1, 2, 4, 8} -- timing `reps` solves per candidate with
- * CUDA events on `stream` after one warm-up solve, and write the fastest into
- * opt->ctas_per_sm / chunk_big / chunk_small (the other fields of *opt are the base
+ * {1, 2, 4}, chunk_small in {1, 2, 4, 8}, team_min_slots (threads per 1-D LP of a
+ * CTA-staged LP: 128 from 512 or 1024 slots on, or always 32) in {512, 1024, 4096} --
+ * timing `reps` solves per candidate with CUDA events on `stream` after one warm-up
+ * solve, and write the fastest into opt->ctas_per_sm / chunk_big / chunk_small /
+ * team_min_slots (the other fields of *opt are the base
  * options of every trial; out_nviol / out_def are not written).  The tuned fields
  * change only the speed: results are the same for every setting.  The arguments
  * are those of lp2d_solve_batch_ex; out_xy / out_status hold the last trial's
@@ -257,6 +266,8 @@ int lp2d_autotune(const float* ax, const float* ay, const float* b, const int64_
 /**
  * Synchronise `stream`, return the device error word accumulated in `workspace`
  * (LP2D_DEVERR_* bits) through *out_bits, and clear it.  Returns an lp2d_err.
+ * (The error word lives in the caller's workspace, not in per-stream library state,
+ * so the call names the workspace as well as the stream.)
  */
 int lp2d_read_device_error(void* workspace, lp2d_stream_t stream, uint32_t* out_bits);
 

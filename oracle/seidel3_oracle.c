@@ -15,7 +15,7 @@
  *   which is Seidel's 2-D method again, whose violations in turn solve 1-D LPs on
  *   lines (Eqs. 3 and 4).  An infeasible 2-D LP makes the 3-D LP infeasible.
  *
- * Readings (the paper is silent on them; each is listed in the design doc):
+ * Readings (the paper is silent on them; R16-R21 of the project's readings):
  *   - box planes have positions -6..-1 in the order x<=xmax, -x<=-xmin, y<=ymax,
  *     -y<=-ymin, z<=zmax, -z<=-zmin, and ids -1..-6;
  *   - the visit order is the 2-D solver's (oracle_perm_array, seed + l);

@@ -16,7 +16,7 @@
  *   infeasible;
  *   dimension 1 is the 1-D LP of Eqs. 3 and 4 over the box and the earlier constraints.
  *
- * Readings (each listed in the design doc):
+ * Readings (R22-R25 of the project's readings):
  *   - box planes have positions -2d..-1 in the order x_0 <= max_0, -x_0 <= -min_0,
  *     x_1 <= max_1, ... and ids -1..-2d;
  *   - the visit order is the 2-D solver's (oracle_perm_array, seed + l);

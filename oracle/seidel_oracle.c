@@ -17,7 +17,7 @@
  *     Eq. 4: u_right = min over right-bounded sigma(h,l); infeasible when the
  *     interval is empty; otherwise the endpoint favoured by the objective).
  *
- * Readings where the paper is silent or ambiguous (each is listed in the design doc):
+ * Readings where the paper is silent or ambiguous (R1-R15 of the project's readings):
  *   - Eq. 3/4 infeasibility: strict u_left > u_right (a single point is feasible).
  *   - objective orthogonal to the line (c.u == 0): take u_left.
  *   - ties in sigma: the earliest visit position wins (box sides first, at

@@ -271,16 +271,20 @@ int lp2d_autotune(const float* ax, const float* ay, const float* b, const int64_
     const int ctas[2] = {occ, occ > 1 ? occ - 1 : occ};
     const int bigs[3] = {1, 2, 4};
     const int smalls[4] = {1, 2, 4, 8};
+    // threads per 1-D LP of a CTA-staged LP: from 512 (or 1024) earlier constraints on
+    // the CTA's 128 threads, or always the driving warp's 32 (4096 exceeds every stage)
+    const int teams[3] = {512, 1024, 4096};
     float best = -1.0f;
     lp2d_options winner = base;
     for (int ci = 0; ci < 2 && rc == LP2D_OK; ++ci) {
         if (ci == 1 && ctas[1] == ctas[0]) break;
         for (int bi = 0; bi < 3 && rc == LP2D_OK; ++bi) {
-            for (int si = 0; si < 4 && rc == LP2D_OK; ++si) {
+            for (int si = 0; si < 4 * 3 && rc == LP2D_OK; ++si) {
                 lp2d_options o = base;
                 o.ctas_per_sm = ctas[ci];
                 o.chunk_big = bigs[bi];
-                o.chunk_small = smalls[si];
+                o.chunk_small = smalls[si % 4];
+                o.team_min_slots = teams[si / 4];
                 rc = lp2d_solve_batch_ex(ax, ay, b, offsets, n_lp, obj_xy, box, out_xy, out_status, &o, workspace,
                                          workspace_bytes, stream);  // warm-up
                 if (rc != LP2D_OK) break;
@@ -309,6 +313,7 @@ int lp2d_autotune(const float* ax, const float* ay, const float* b, const int64_
     opt->ctas_per_sm = winner.ctas_per_sm;
     opt->chunk_big = winner.chunk_big;
     opt->chunk_small = winner.chunk_small;
+    opt->team_min_slots = winner.team_min_slots;
     if (out_best_ms) *out_best_ms = best;
     return ok();
 }
@@ -342,6 +347,7 @@ namespace {
 // host-to-device copies and the events that order them against the solves, which run
 // with their device-to-host copies on the caller's stream.
 struct HostPipe {
+    std::mutex mu;  // held for a whole call: calls on one (device, stream) run one at a time
     char* dev = nullptr;
     size_t slot_bytes = 0;
     cudaStream_t copy = nullptr;
@@ -422,8 +428,12 @@ int lp2d_solve_batch_host(const float* ax, const float* ay, const float* b, cons
     const cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     HostPipe* pp = nullptr;
     {
-        std::lock_guard<std::mutex> lock(g_mu);
-        HostPipe& p = g_pipes[std::make_pair(dev, cs)];
+        std::lock_guard<std::mutex> lock(g_mu);  // map nodes stay where they are once inserted
+        pp = &g_pipes[std::make_pair(dev, cs)];
+    }
+    HostPipe& p = *pp;
+    std::lock_guard<std::mutex> pipe_lock(p.mu);
+    {
         if (!p.copy) {
             if ((e = cudaStreamCreateWithFlags(&p.copy, cudaStreamNonBlocking)) != cudaSuccess)
                 return fail(LP2D_ERR_CUDA, "copy stream: %s", cudaGetErrorString(e));
@@ -448,9 +458,7 @@ int lp2d_solve_batch_host(const float* ax, const float* ay, const float* b, cons
                 return fail(LP2D_ERR_CUDA, "pipeline memset: %s", cudaGetErrorString(e));
             p.slot_bytes = need;
         }
-        pp = &p;
     }
-    HostPipe& p = *pp;
     // copies of a call start after the caller's earlier work on its stream
     if ((e = cudaEventRecord(p.entry, cs)) != cudaSuccess || (e = cudaStreamWaitEvent(p.copy, p.entry, 0)) != cudaSuccess)
         return fail(LP2D_ERR_CUDA, "ordering: %s", cudaGetErrorString(e));
@@ -480,9 +488,15 @@ int lp2d_solve_batch_host(const float* ax, const float* ay, const float* b, cons
         if ((e = cudaStreamWaitEvent(cs, p.in_ready[s], 0)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(dws, 0, sizeof(unsigned long long) * lp2d::kWsWords, cs)) != cudaSuccess) break;
         // offsets stay absolute: the constraint arrays are passed shifted back by c0
+        // element addresses (in integer arithmetic: the shifted address lies outside the
+        // slot, and the kernels only ever add offsets >= c0 to it)
         lp2d_options oc = opt;
         oc.seed = opt.seed + static_cast<uint64_t>(lo);
-        const int rc = lp2d_solve_batch_ex(dax - c0, day - c0, db - c0, doff, n, dobj, box, dxy, dst, &oc, dws,
+        auto back = [c0](const float* q) {
+            return reinterpret_cast<const float*>(reinterpret_cast<uintptr_t>(q) -
+                                                  static_cast<uintptr_t>(c0) * sizeof(float));
+        };
+        const int rc = lp2d_solve_batch_ex(back(dax), back(day), back(db), doff, n, dobj, box, dxy, dst, &oc, dws,
                                            up256(sizeof(unsigned long long) * lp2d::kWsWords), stream);
         if (rc != LP2D_OK) return rc;
         // results (12 bytes per LP) go back on the solve stream, so the copy stream never

@@ -50,6 +50,9 @@ extern "C" int lp2d_solve_batch_noalloc(const float* ax, const float* ay, const 
 
     // Set-up, once per device with that device current: the array's name is a host-side
     // stand-in in host code, so the kernel gets the device address from the runtime.
+    // The cached address belongs to the device's current context: after a
+    // cudaDeviceReset it is stale, and the process must not call this entry point on
+    // that device again.
     void* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mu);

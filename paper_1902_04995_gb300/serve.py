@@ -14,6 +14,11 @@ Layout of a request in the arena (and in its pinned host payload), each array
 aligned to 256 bytes: ax, ay, b (float32 [n_c]), offsets (int64 [n_lp + 1]), obj
 (float32 [2 n_lp]); then the results xy (float32 [2 n_lp]) and status (int32 [n_lp]),
 and the 256-byte solver workspace.
+
+Requests on resident data (ResidentPool, try_submit_resident): the LPs are placed in
+device memory once and a request names a range of them with its own seed, so only
+the results (12 bytes per LP) cross the host link; the arena then holds only each
+request's results and workspace, and the results land in a pinned host ring.
 """
 from __future__ import annotations
 
@@ -149,13 +154,18 @@ class ServeEngine:
 
     def __init__(self, capacity_bytes: int = 20 << 30, n_streams: int = 4, device="cuda",
                  options: lp2d.Options | None = None):
+        self.options = options if options is not None else lp2d.default_options()
+        if self.options.precision == lp2d.PREC_FP64:
+            # the request layout holds float32 vertices; FP64 callers use solve_batch_ex
+            raise ValueError("ServeEngine serves the FP32 precisions only")
         self.device = torch.device(device)
         self.arena = torch.empty(int(capacity_bytes), dtype=torch.uint8, device=self.device)
         self.alloc = ArenaAllocator(capacity_bytes)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(n_streams)]
         self.load = [0] * n_streams
-        self.options = options if options is not None else lp2d.default_options()
         self.inflight: list[_InFlight] = []
+        self.host_out = None  # pinned result ring of the resident requests (make_host_ring)
+        self.host_alloc = None
         self._next_id = 0
 
     def _view(self, start, off, name, dtype, count):
@@ -193,6 +203,97 @@ class ServeEngine:
         self.inflight.append(_InFlight(self._next_id, payload, arrival, time.perf_counter(), start, size, ev, si))
         self._next_id += 1
         return True
+
+    # ---- requests on device-resident data
+    def make_host_ring(self, nbytes: int):
+        """Pinned host memory that the results of resident requests are copied into
+        (first-fit, freed when a request retires)."""
+        self.host_out = torch.empty(int(nbytes), dtype=torch.uint8).pin_memory()
+        self.host_alloc = ArenaAllocator(int(nbytes))
+
+    def try_submit_resident(self, pool: "ResidentPool", req: "ResidentRequest", arrival: float) -> bool:
+        """Admit a request on LPs already resident in device memory: only its results
+        and workspace take arena memory, and only its results cross the host link."""
+        n_lp = req.hi - req.lo
+        xy_b, st_b, ws_b = _up(8 * n_lp), _up(4 * n_lp), _up(lp2d.workspace_bytes(n_lp))
+        got = self.alloc.alloc(xy_b + st_b + ws_b)
+        if got is None:
+            return False
+        hgot = self.host_alloc.alloc(xy_b + st_b)
+        if hgot is None:
+            self.alloc.release(*got)
+            return False
+        start, size = got
+        si = min(range(len(self.streams)), key=lambda i: self.load[i])
+        s = self.streams[si]
+        t = pool.t
+        with torch.cuda.stream(s):
+            ws = self.arena[start + xy_b + st_b:start + xy_b + st_b + ws_b]
+            lp2d.workspace_init(ws, stream=s)
+            opts = lp2d.Options.from_buffer_copy(self.options)
+            opts.seed = req.seed
+            xy = self.arena[start:start + 8 * n_lp].view(torch.float32)
+            st = self.arena[start + xy_b:start + xy_b + 4 * n_lp].view(torch.int32)
+            lp2d.solve_batch_ex(t["ax"], t["ay"], t["b"], t["offsets"][req.lo:req.hi + 1],
+                                t["obj"][2 * req.lo:2 * req.hi], pool.box, xy, st, opts, ws, stream=s)
+            self.host_out[hgot[0]:hgot[0] + xy_b + st_b].copy_(self.arena[start:start + xy_b + st_b],
+                                                                 non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        self.load[si] += size
+        r = _InFlight(self._next_id, req, arrival, time.perf_counter(), start, size, ev, si)
+        r.host = hgot
+        self.inflight.append(r)
+        self._next_id += 1
+        return True
+
+    def resident_results(self, r):
+        """(xy float32 [n_lp, 2], status int32 [n_lp]) of a retired resident request,
+        from the host ring (valid until the ring range is reused)."""
+        n_lp = r.payload.hi - r.payload.lo
+        h = self.host_out.numpy()[r.host[0]:r.host[0] + r.host[1]]
+        xy = h[:8 * n_lp].view(np.float32).reshape(-1, 2)
+        st = h[_up(8 * n_lp):_up(8 * n_lp) + 4 * n_lp].view(np.int32)
+        return xy.copy(), st.copy()
+
+    def run_resident_stream(self, pool, requests, arrivals, max_wall_s: float = 120.0,
+                            keep_results: bool = False) -> ServeStats:
+        """Serve resident requests[i] arriving at arrivals[i] seconds, in order of
+        arrival; latency = results in host memory minus arrival."""
+        stats = ServeStats()
+        t0 = time.perf_counter()
+        pending = 0
+        n = len(requests)
+        self.results = {}
+        while (pending < n or self.inflight) and time.perf_counter() - t0 < max_wall_s:
+            now = time.perf_counter() - t0
+            while pending < n and arrivals[pending] <= now:
+                if not self.try_submit_resident(pool, requests[pending], t0 + arrivals[pending]):
+                    break
+                pending += 1
+            for r, t_done in self._poll_records():
+                stats.latencies_ms.append(1e3 * (t_done - r.arrival))
+                stats.lps += r.payload.hi - r.payload.lo
+                stats.requests += 1
+                if keep_results:
+                    self.results[r.rid] = self.resident_results(r)
+                self.host_alloc.release(*r.host)
+        stats.wall_s = time.perf_counter() - t0
+        stats.peak_bytes = self.alloc.peak + pool.bytes
+        return stats
+
+    def _poll_records(self):
+        done, keep = [], []
+        for r in self.inflight:
+            if r.done.query():
+                t = time.perf_counter()
+                self.alloc.release(r.start, r.size)
+                self.load[r.stream_idx] -= r.size
+                done.append((r, t))
+            else:
+                keep.append(r)
+        self.inflight = keep
+        return done
 
     def poll(self):
         """Retire finished requests: free their memory; return [(rid, payload, arrival, t_done)]."""
@@ -234,6 +335,39 @@ class ServeEngine:
         stats.wall_s = time.perf_counter() - t0
         stats.peak_bytes = self.alloc.peak
         return stats
+
+
+class ResidentPool:
+    """LPs placed in device memory once; requests name ranges of them (the serving
+    case where a request picks a payload that is already resident)."""
+
+    def __init__(self, batch, device="cuda"):
+        dev = torch.device(device)
+        self.t = {k: torch.from_numpy(np.ascontiguousarray(batch[k])).to(dev).reshape(-1)
+                  for k in ("ax", "ay", "b", "offsets", "obj")}
+        self.offsets = np.asarray(batch["offsets"])
+        self.n_lp = int(len(self.offsets) - 1)
+        self.box = tuple(batch["box"])
+        self.bytes = int(sum(v.numel() * v.element_size() for v in self.t.values()))
+
+
+@dataclass
+class ResidentRequest:
+    lo: int    # first LP of the pool
+    hi: int    # one past the last
+    seed: int
+
+
+def resident_requests(pool: ResidentPool, n_distinct: int, seed: int, lo_lp=1024, hi_lp=65536):
+    """n_distinct requests: a log-uniform number of LPs in [lo_lp, hi_lp] starting at a
+    uniform LP of the pool, each with its own seed."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_distinct):
+        n = int(min(np.floor(np.exp(rng.uniform(np.log(lo_lp), np.log(hi_lp + 1)))), pool.n_lp))
+        lo = int(rng.integers(0, pool.n_lp - n + 1))
+        out.append(ResidentRequest(lo, lo + n, seed + 1000 * i))
+    return out
 
 
 def poisson_arrivals(rate_per_s: float, duration_s: float, seed: int):

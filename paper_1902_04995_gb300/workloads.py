@@ -267,6 +267,13 @@ def collision(seed=DEFAULT_SEED, n_lp=16384):
     return collision_batch(n_lp, seed=seed)
 
 
+def serving_pool(seed=DEFAULT_SEED, n_lp=65536, lo_m=16, hi_m=4096):
+    """LPs that resident serving requests draw their ranges from: sizes log-uniform
+    in [lo_m, hi_m] as in serving_request, disk family, 10 % infeasible."""
+    rng = np.random.default_rng(seed)
+    return disk_batch(loguniform_sizes(rng, n_lp, lo_m, hi_m), seed=seed, infeasible_frac=0.1)
+
+
 def serving_request(seed, lo_lp=1024, hi_lp=65536, lo_m=16, hi_m=4096):
     """One serving request: log-uniform [1k, 64k] LPs with sizes log-uniform in
     [16, 4096], the ragged generator, 10 % infeasible."""

@@ -225,6 +225,7 @@ def test_autotune_picks_a_grid_point_and_keeps_the_results():
     o = solver.options
     assert ms > 0.0
     assert o.chunk_big in (1, 2, 4) and o.chunk_small in (1, 2, 4, 8) and o.ctas_per_sm >= 1
+    assert o.team_min_slots in (512, 1024, 4096)
     solver(t["ax"], t["ay"], t["b"], t["offsets"], t["obj"].reshape(-1), batch["box"])
     torch.cuda.synchronize()
     assert (solver.out_status.cpu().numpy() == base["status"]).all()

@@ -108,3 +108,56 @@ def test_admission_waits_for_memory(serve_mod):
     assert stats.peak_bytes <= 2 * biggest + 4096
     s = stats.summary()
     assert s["p99_ms"] >= s["p50_ms"] > 0
+
+
+def test_engine_rejects_fp64_options(serve_mod):
+    # the request layout holds float32 vertices: FP64 options are refused before
+    # anything is allocated
+    from paper_1902_04995_gb300 import lp2d
+
+    with pytest.raises(ValueError):
+        serve_mod.ServeEngine(capacity_bytes=1 << 20, options=lp2d.default_options(precision=lp2d.PREC_FP64),
+                              device="cpu")
+
+
+def test_resident_requests_cover_the_pool(serve_mod):
+    class Pool:  # the pool's shape is all resident_requests reads
+        n_lp = 5000
+
+    reqs = serve_mod.resident_requests(Pool(), 64, seed=3, lo_lp=16, hi_lp=4096)
+    assert len({(r.lo, r.hi, r.seed) for r in reqs}) == 64
+    assert all(0 <= r.lo < r.hi <= 5000 and 16 <= r.hi - r.lo <= 4096 for r in reqs)
+
+
+@pytest.mark.gpu
+def test_resident_results_same_alone_and_in_the_mix(serve_mod):
+    # requests on device-resident LPs: byte-identical results alone and overlapping on
+    # 4 streams, equal to one direct solve of the same range with the same seed
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1902_04995_gb300 import lp2d
+
+    batch = workloads.serving_pool(seed=9, n_lp=8192, hi_m=1500)
+    pool = serve_mod.ResidentPool(batch)
+    reqs = serve_mod.resident_requests(pool, 12, seed=5, lo_lp=256, hi_lp=4096)
+    eng = serve_mod.ServeEngine(capacity_bytes=1 << 30, n_streams=4)
+    eng.make_host_ring(64 << 20)
+    mixed = eng.run_resident_stream(pool, reqs, np.zeros(len(reqs)), keep_results=True)
+    assert mixed.requests == len(reqs)
+    mix = [eng.results[i] for i in range(len(reqs))]
+    alone = eng.run_resident_stream(pool, reqs, np.arange(len(reqs)) * 0.05, keep_results=True)
+    assert alone.requests == len(reqs)
+    for i, r in enumerate(reqs):
+        xy, st = eng.results[len(reqs) + i]
+        assert (st == mix[i][1]).all()
+        assert np.array_equal(xy, mix[i][0], equal_nan=True)
+        n = r.hi - r.lo
+        t = pool.t
+        dxy = torch.empty(2 * n, device="cuda")
+        dst = torch.empty(n, dtype=torch.int32, device="cuda")
+        opts = lp2d.default_options(seed=r.seed)
+        lp2d.solve_batch_ex(t["ax"], t["ay"], t["b"], t["offsets"][r.lo:r.hi + 1], t["obj"][2 * r.lo:2 * r.hi],
+                            pool.box, dxy, dst, opts, lp2d.new_workspace(n, opts, device="cuda"))
+        torch.cuda.synchronize()
+        assert (dst.cpu().numpy() == st).all()
+        assert np.array_equal(dxy.cpu().numpy().reshape(-1, 2), xy, equal_nan=True)
