@@ -34,8 +34,10 @@
 extern "C" {
 #endif
 
-/** Largest LP the 3-D solver stages (1024 stage slots less the six box planes). */
-#define LP3D_MAX_CONSTRAINTS 1018
+/** Largest LP the 3-D solver stages: LPs of up to 1018 constraints share a CTA's stage
+    (1024 slots less the six box planes per warp); larger ones go to a one-warp kernel
+    with a 12288-slot stage in dynamic shared memory (12288 less the six box planes). */
+#define LP3D_MAX_CONSTRAINTS 12282
 
 /** The bounding box (finite, min < max on every axis); the box planes have visit
  *  positions -6..-1 in the order x <= xmax, -x <= -xmin, y <= ymax, -y <= -ymin,

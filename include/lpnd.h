@@ -40,9 +40,10 @@ extern "C" {
 /** Largest dimension the solver is built for. */
 #define LPND_MAX_DIM 5
 
-/** Largest LP the d-dimensional solver stages (1024 stage slots less the 2d box
- *  planes). */
-#define LPND_MAX_CONSTRAINTS(d) (1024 - 2 * (d))
+/** Largest LP the d-dimensional solver stages: LPs of up to 1024 - 2d constraints
+ *  share a CTA's stage (1024 slots per warp, less the 2d box planes); larger ones go to
+ *  a one-warp kernel with an 8192-slot stage in dynamic shared memory. */
+#define LPND_MAX_CONSTRAINTS(d) (8192 - 2 * (d))
 
 /**
  * Solve a batch of d-dimensional LPs, 2 <= d <= LPND_MAX_DIM.

@@ -16,15 +16,22 @@
 //   - an infeasible 2-D LP makes the LP infeasible.
 // A persistent grid of 4-warp CTAs pulls LPs from two queues: LPs of 507..1018
 // constraints go to warps 0 and 1 with half of the CTA's stage each, smaller ones to
-// all four warps with a quarter each.  Larger LPs are reported as BAD_INPUT.
+// all four warps with a quarter each.  A second, one-warp-per-CTA kernel launched
+// after it takes the LPs of 1019..12282 constraints from a third queue, each staged
+// in about 200 KB of dynamic shared memory; larger LPs are reported as BAD_INPUT.
 #include <cstdarg>
 #include <cstdio>
 
+#include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "lp3d.h"
 #include "lp2d_internal.h"
 #include "lp2d_staged.cuh"
+#include "lp_stage_big.cuh"
 
 namespace lp2d {
 
@@ -36,6 +43,13 @@ constexpr int kCap3Mid = kHalf3 - kBox3;
 constexpr int kStage3 = 4 * kQuarter3;
 constexpr int kWarps3 = 4;
 constexpr unsigned kDevErrTooLarge = 4u;
+// The large-LP kernel: one warp per CTA, a stage of kStage3L slots per array and a key
+// bitmap for domains up to 4^7 = 16384 bits, in dynamic shared memory.
+constexpr int kStage3L = 12288;
+constexpr int kCap3Large = kStage3L - kBox3;
+constexpr int kWords3L = 512;
+constexpr size_t kSmem3L = sizeof(float) * 4 * kStage3L + sizeof(unsigned) * kWords3L + sizeof(int) * kWords3L;
+constexpr int kWsDoneLarge = 5;  // workspace word: large-LP CTAs that have finished
 
 struct Params3 {
     const float* __restrict__ ax;
@@ -342,9 +356,10 @@ __device__ __forceinline__ void write_bad3(const Params3& P, int64_t lp, unsigne
 // One warp's loop over a queue: grab spans of LP indices (doubling after a grab
 // without LPs of the class, halving after one with more than the target), stage and
 // solve the LPs of size (lo, hi] among them.
-template <typename Real>
+template <typename Real, bool kLarge = false>
 __device__ void warp_queue3(const Params3& P, unsigned long long* head, long long lo, long long hi, float* sX,
-                            float* sY, float* sZ, float* sB, unsigned* bm, int lane) {
+                            float* sY, float* sZ, float* sB, unsigned* bm, int lane, int* pre = nullptr) {
+    constexpr long long kCap = kLarge ? kCap3Large : kCap3Mid;
     int span = P.chunk;
     for (;;) {
         long long start = 0;
@@ -367,7 +382,7 @@ __device__ void warp_queue3(const Params3& P, unsigned long long* head, long lon
             const int64_t lp = start + i;
             const long long base = __shfl_sync(kFull, off_l, i);
             const long long mm = __shfl_sync(kFull, mm_l, i);
-            if (mm < 0 || mm > kCap3Mid) {
+            if (mm < 0 || mm > kCap) {
                 if (lane == 0) write_bad3<Real>(P, lp, mm < 0 ? kDevErrBadOffsets : kDevErrTooLarge);
                 continue;
             }
@@ -375,8 +390,22 @@ __device__ void warp_queue3(const Params3& P, unsigned long long* head, long lon
             VisitOrder vo;
             warp_visit_order(vo, P.seed + static_cast<uint64_t>(lp), static_cast<uint32_t>(m), lane);
             write_box3(P, sX, sY, sZ, sB, lane);
-            stage_lp3_warp(vo, m, P.ax + base, P.ay + base, P.az ? P.az + base : nullptr, P.b + base, sX, sY, sZ,
-                           sB, bm, lane);
+            if constexpr (kLarge) {
+                const float* gax = P.ax + base;
+                const float* gay = P.ay + base;
+                const float* gaz = P.az ? P.az + base : nullptr;
+                const float* gb = P.b + base;
+                stage_ranks_warp(vo, m, bm, pre, lane, [&](int r, int q) {
+                    const int slot = kBox3 + r;
+                    cp_async4(sX + slot, gax + q);
+                    cp_async4(sY + slot, gay + q);
+                    if (gaz) cp_async4(sZ + slot, gaz + q);
+                    cp_async4(sB + slot, gb + q);
+                });
+            } else {
+                stage_lp3_warp(vo, m, P.ax + base, P.ay + base, P.az ? P.az + base : nullptr, P.b + base, sX, sY,
+                               sZ, sB, bm, lane);
+            }
             cp_async_wait_all();
             __syncwarp();
             if (P.az == nullptr) {
@@ -404,9 +433,9 @@ __global__ void __launch_bounds__(kWarps3 * 32, sizeof(Real) == 4 ? 6 : 1) seide
     __shared__ unsigned s_bm[kWarps3 * 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned long long* ws = P.ws;
-    // mid-size LPs (and those too large or with bad sizes): warps 0 and 1, half a stage each
+    // mid-size LPs: warps 0 and 1, half a stage each
     if (warp < 2)
-        warp_queue3<Real>(P, ws + kWsHeadMid, kCap3Small, 1ll << 62, sX + warp * kHalf3, sY + warp * kHalf3,
+        warp_queue3<Real>(P, ws + kWsHeadMid, kCap3Small, kCap3Mid, sX + warp * kHalf3, sY + warp * kHalf3,
                           sZ + warp * kHalf3, sB + warp * kHalf3, s_bm + warp * 32, lane);
     __syncthreads();
     // small LPs (and negative sizes): every warp, a quarter of the stage each
@@ -421,6 +450,31 @@ __global__ void __launch_bounds__(kWarps3 * 32, sizeof(Real) == 4 ? 6 : 1) seide
             atomicExch(ws + kWsHeadMid, 0ull);
             atomicExch(ws + kWsHeadSmall, 0ull);
             atomicExch(ws + kWsDone, 0ull);
+        }
+    }
+}
+
+// LPs above kCap3Mid constraints: one warp per CTA with a stage of kStage3L slots;
+// LPs above kCap3Large are reported as too large.  Runs after seidel3_kernel on the
+// same stream, with its own queue head and done counter.
+template <typename Real>
+__global__ void __launch_bounds__(32, 1) seidel3_large_kernel(const Params3 P) {
+    extern __shared__ __align__(16) unsigned char smem3l[];
+    float* sX = reinterpret_cast<float*>(smem3l);
+    float* sY = sX + kStage3L;
+    float* sZ = sY + kStage3L;
+    float* sB = sZ + kStage3L;
+    unsigned* bm = reinterpret_cast<unsigned*>(sB + kStage3L);
+    int* pre = reinterpret_cast<int*>(bm + kWords3L);
+    const int lane = threadIdx.x;
+    unsigned long long* ws = P.ws;
+    warp_queue3<Real, true>(P, ws + kWsHeadBig, kCap3Mid, 1ll << 62, sX, sY, sZ, sB, bm, lane, pre);
+    if (lane == 0) {
+        __threadfence();
+        const unsigned long long prev = atomicAdd(ws + kWsDoneLarge, 1ull);
+        if (prev == static_cast<unsigned long long>(gridDim.x) - 1ull) {
+            atomicExch(ws + kWsHeadBig, 0ull);
+            atomicExch(ws + kWsDoneLarge, 0ull);
         }
     }
 }
@@ -449,6 +503,26 @@ int occupancy3(bool fp64, int* sms, int* per_sm) {
 
 namespace {
 
+// Opt the large-LP kernel in to its dynamic shared memory, once per device and precision.
+std::mutex g_large3_mu;
+std::set<std::pair<int, bool>> g_large3_ready;
+
+int large3_ready(bool fp64) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return lp2d::report_error(LP2D_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    std::lock_guard<std::mutex> lock(g_large3_mu);
+    if (g_large3_ready.count({dev, fp64})) return LP2D_OK;
+    e = fp64 ? cudaFuncSetAttribute(lp2d::seidel3_large_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(lp2d::kSmem3L))
+             : cudaFuncSetAttribute(lp2d::seidel3_large_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(lp2d::kSmem3L));
+    if (e != cudaSuccess)
+        return lp2d::report_error(LP2D_ERR_CUDA, "large-LP kernel shared memory: %s", cudaGetErrorString(e));
+    g_large3_ready.insert({dev, fp64});
+    return LP2D_OK;
+}
+
 int launch3(lp2d::Params3& p, const lp2d_options& opt, int64_t n_lp, lp2d_stream_t stream) {
     using lp2d::report_error;
     const bool fp64 = opt.precision == LP2D_PREC_FP64;
@@ -465,6 +539,14 @@ int launch3(lp2d::Params3& p, const lp2d_options& opt, int64_t n_lp, lp2d_stream
     else lp2d::seidel3_kernel<float><<<static_cast<int>(grid), lp2d::kWarps3 * 32, 0, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return report_error(LP2D_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    // LPs above the stage of a warp pair: one CTA per SM, each a warp with ~200 KB
+    rc = large3_ready(fp64);
+    if (rc != LP2D_OK) return rc;
+    const int lgrid = static_cast<int>(std::min<long long>(sms, n_lp));
+    if (fp64) lp2d::seidel3_large_kernel<double><<<lgrid, 32, lp2d::kSmem3L, s>>>(p);
+    else lp2d::seidel3_large_kernel<float><<<lgrid, 32, lp2d::kSmem3L, s>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return report_error(LP2D_ERR_CUDA, "large-LP kernel launch: %s", cudaGetErrorString(e));
     return LP2D_OK;
 }
 

@@ -24,12 +24,14 @@
 // A persistent grid of 4-warp CTAs pulls LPs from two queues: LPs of more than
 // 512 - 2d constraints go to warps 0 and 1 with half of the CTA's stage each, smaller
 // ones to all four warps with a quarter each.  LPs above 1024 - 2d are BAD_INPUT.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
 #include "lpnd.h"
 #include "lp2d_internal.h"
 #include "lp2d_staged.cuh"
+#include "lp_stage_big.cuh"
 
 namespace lp2d {
 
@@ -80,9 +82,10 @@ template <int D, typename Real> constexpr int min_ctas_n() {
 }
 
 // One warp's view of the LP it solves.  x and c are uniform across the warp.
-template <typename Real, int D>
+template <typename Real, int D, int S = kStageN>
 struct WarpN {
-    const float* s;  // coefficient t of slot i at s[t * kStageN + i], b at s[D * kStageN + i]
+    static constexpr int kS = S;  // slots per array of the stage
+    const float* s;  // coefficient t of slot i at s[t * S + i], b at s[D * S + i]
     Real* fr;        // frames of levels 1..D-1
     int* defs;       // slots of the D constraints through x; level k owns defs[D-k .. D-1]
     Real c[D];
@@ -92,13 +95,13 @@ struct WarpN {
     int nviol;
 };
 
-template <typename Real, int D>
+template <typename Real, int D, int S>
 __device__ __forceinline__ bool violates_n(const float* s, int sl, const Real (&x)[D], Real eps) {
-    const Real gb = s[D * kStageN + sl];
+    const Real gb = s[D * S + sl];
     Real acc = -gb, tol = real_abs(gb);
 #pragma unroll
     for (int t = 0; t < D; ++t) {
-        const Real pr = Real(s[t * kStageN + sl]) * x[t];
+        const Real pr = Real(s[t * S + sl]) * x[t];
         acc += pr;
         tol += real_abs(pr);
     }
@@ -174,12 +177,13 @@ __device__ __forceinline__ unsigned nth_mask(int rank) {
 
 // Start of a sub-LP on the level-K frame (2 <= K < D): the best vertex of the box in
 // the subspace.  Sets x and defs[D-K .. D-1]; false if the subspace misses the box.
-template <typename Real, int D, int K>
-__device__ __forceinline__ bool box_start(WarpN<Real, D>& W) {
+template <typename Real, int D, int K, typename WT>
+__device__ __forceinline__ bool box_start(WT& W) {
     using KT = KeyOf<Real>;
+    constexpr int S = WT::kS;
     constexpr int kCands = binom(D, K) << K;
     const Real* F = W.fr + frame_off<D>(K);
-    const float* sb = W.s + D * kStageN;  // slot 2a: b = max_a; slot 2a + 1: b = -min_a
+    const float* sb = W.s + D * S;  // slot 2a: b = max_a; slot 2a + 1: b = -min_a
     bool found = false;
     Real best = Real(0);
     unsigned best_mask = 0u;
@@ -258,13 +262,14 @@ __device__ __forceinline__ bool box_start(WarpN<Real, D>& W) {
 // The level-(K-1) frame: the hyperplane of slot f inside the level-K subspace (the
 // whole space, p = 0 and E = I, when K == D).  False if g's normal is orthogonal to
 // the subspace (then the violated g excludes all of it).
-template <typename Real, int D, int K>
-__device__ __forceinline__ bool child_frame(WarpN<Real, D>& W, int f) {
+template <typename Real, int D, int K, typename WT>
+__device__ __forceinline__ bool child_frame(WT& W, int f) {
+    constexpr int S = WT::kS;
     const Real* F = W.fr + frame_off<D>(K < D ? K : 1);
     Real g[D];
 #pragma unroll
-    for (int t = 0; t < D; ++t) g[t] = W.s[t * kStageN + f];
-    Real r = W.s[D * kStageN + f];
+    for (int t = 0; t < D; ++t) g[t] = W.s[t * S + f];
+    Real r = W.s[D * S + f];
     Real A[K];
     if constexpr (K == D) {
 #pragma unroll
@@ -322,8 +327,9 @@ __device__ __forceinline__ bool child_frame(WarpN<Real, D>& W, int f) {
 // The LP on the level-K subspace over the stage slots 0..limit-1 (the box and the
 // constraints visited before slot limit).  Level D starts from the current x (the
 // box corner); lower levels find their own start.  False if infeasible.
-template <typename Real, int D, int K>
-__device__ __forceinline__ bool solve_level(WarpN<Real, D>& W, int limit) {
+template <typename Real, int D, int K, typename WT>
+__device__ __forceinline__ bool solve_level(WT& W, int limit) {
+    constexpr int S = WT::kS;
     if constexpr (K == 1) {
         // Eqs. 3, 4 on the line p + t e, e oriented so that the objective's end is the
         // right end (the left end of E_0 when c is perpendicular to the line)
@@ -342,10 +348,10 @@ __device__ __forceinline__ bool solve_level(WarpN<Real, D>& W, int limit) {
         const Real ninf = -real_inf<Real>();
         int phi = kNoPos;
         for (int f = W.lane; f < limit; f += 32) {
-            Real num = W.s[D * kStageN + f], den = Real(0);
+            Real num = W.s[D * S + f], den = Real(0);
 #pragma unroll
             for (int t = 0; t < D; ++t) {
-                const Real gt = W.s[t * kStageN + f];
+                const Real gt = W.s[t * S + f];
                 num -= gt * p[t];
                 den += gt * e[t];
             }
@@ -370,7 +376,7 @@ __device__ __forceinline__ bool solve_level(WarpN<Real, D>& W, int limit) {
         int k = 2 * D;
         while (k < limit) {
             const int q = k + W.lane;
-            const bool v = q < limit && violates_n<Real, D>(W.s, q, W.x, W.eps);
+            const bool v = q < limit && violates_n<Real, D, S>(W.s, q, W.x, W.eps);
             const unsigned bal = __ballot_sync(kFull, v);
             if (bal == 0u) {
                 k += 32;
@@ -387,7 +393,7 @@ __device__ __forceinline__ bool solve_level(WarpN<Real, D>& W, int limit) {
     }
 }
 
-template <int D>
+template <int D, int S = kStageN>
 __device__ __forceinline__ void write_box_n(const ParamsN& P, float* s, int lane) {
     if (lane < 2 * D) {
         const int axis = lane >> 1;
@@ -395,10 +401,10 @@ __device__ __forceinline__ void write_box_n(const ParamsN& P, float* s, int lane
         float bv = 0.0f;
 #pragma unroll
         for (int t = 0; t < D; ++t) {
-            s[t * kStageN + lane] = (t == axis) ? sg : 0.0f;
+            s[t * S + lane] = (t == axis) ? sg : 0.0f;
             if (t == axis) bv = (lane & 1) ? -P.box[2 * t] : P.box[2 * t + 1];
         }
-        s[D * kStageN + lane] = bv;
+        s[D * S + lane] = bv;
     }
 }
 
@@ -457,10 +463,10 @@ __device__ __forceinline__ void write_bad_n(const ParamsN& P, int64_t lp, unsign
 }
 
 // Seidel's method on one staged LP by one warp; writes the LP's outputs.
-template <typename Real, int D>
+template <typename Real, int D, int S = kStageN>
 __device__ void drive_lp_n(const ParamsN& P, int64_t lp, int m, const VisitOrder& vo, const float* s, Real* fr,
                            int* defs, const unsigned* bm, int lane) {
-    WarpN<Real, D> W;
+    WarpN<Real, D, S> W;
     W.s = s;
     W.fr = fr;
     W.defs = defs;
@@ -480,7 +486,7 @@ __device__ void drive_lp_n(const ParamsN& P, int64_t lp, int m, const VisitOrder
         bool nf = false;
         for (int i = lane; i < m; i += 32)
 #pragma unroll
-            for (int t = 0; t <= D; ++t) nf |= !(fabsf(s[t * kStageN + 2 * D + i]) <= 3.402823466e38f);
+            for (int t = 0; t <= D; ++t) nf |= !(fabsf(s[t * S + 2 * D + i]) <= 3.402823466e38f);
         bad |= __any_sync(kFull, nf);
     }
     __syncwarp();
@@ -518,10 +524,10 @@ __device__ void drive_lp_n(const ParamsN& P, int64_t lp, int m, const VisitOrder
 // One warp's loop over a queue: grab spans of LP indices (doubling after a grab
 // without LPs of the class, halving after one with more than the target), stage and
 // solve the LPs of size (lo, hi] among them.
-template <typename Real, int D>
+template <typename Real, int D, int S = kStageN, bool kLarge = false>
 __device__ void warp_queue_n(const ParamsN& P, unsigned long long* head, long long lo, long long hi, float* s,
-                             Real* fr, int* defs, unsigned* bm, int lane) {
-    constexpr int kCap = kHalfN - 2 * D;
+                             Real* fr, int* defs, unsigned* bm, int lane, int* pre = nullptr) {
+    constexpr int kCap = (kLarge ? S : kHalfN) - 2 * D;
     int span = P.chunk;
     for (;;) {
         long long start = 0;
@@ -550,11 +556,20 @@ __device__ void warp_queue_n(const ParamsN& P, unsigned long long* head, long lo
             const int m = static_cast<int>(mm);
             VisitOrder vo;
             warp_visit_order(vo, P.seed + static_cast<uint64_t>(lp), static_cast<uint32_t>(m), lane);
-            write_box_n<D>(P, s, lane);
-            stage_lp_n<D>(P, vo, m, base, s, bm, lane);
+            write_box_n<D, S>(P, s, lane);
+            if constexpr (kLarge) {
+                stage_ranks_warp(vo, m, bm, pre, lane, [&](int r, int q) {
+                    const int slot = 2 * D + r;
+#pragma unroll
+                    for (int t = 0; t < D; ++t) cp_async4(s + t * S + slot, P.a[t] + base + q);
+                    cp_async4(s + D * S + slot, P.b + base + q);
+                });
+            } else {
+                stage_lp_n<D>(P, vo, m, base, s, bm, lane);
+            }
             cp_async_wait_all();
             __syncwarp();
-            drive_lp_n<Real, D>(P, lp, m, vo, s, fr, defs, bm, lane);
+            drive_lp_n<Real, D, S>(P, lp, m, vo, s, fr, defs, bm, lane);
             __syncwarp();  // all lanes are done with the stage before it is overwritten
         }
     }
@@ -572,10 +587,10 @@ __global__ void __launch_bounds__(kWarpsN * 32, (min_ctas_n<D, Real>())) seidel_
     Real* fr = frames + warp * kFrameReals<D>;
     int* df = defs + warp * D;
     unsigned* bm = bms + warp * 32;
-    // mid-size LPs (and those too large or with bad sizes): warps 0 and 1, half a stage each
+    // mid-size LPs: warps 0 and 1, half a stage each
     if (warp < 2)
-        warp_queue_n<Real, D>(P, ws + kWsHeadMid, kQuarterN - 2 * D, 1ll << 62, stage + warp * kHalfN, fr, df, bm,
-                              lane);
+        warp_queue_n<Real, D>(P, ws + kWsHeadMid, kQuarterN - 2 * D, kHalfN - 2 * D, stage + warp * kHalfN, fr, df,
+                              bm, lane);
     __syncthreads();
     // small LPs (and negative sizes): every warp, a quarter of the stage each
     warp_queue_n<Real, D>(P, ws + kWsHeadSmall, -(1ll << 62), kQuarterN - 2 * D, stage + warp * kQuarterN, fr, df,
@@ -589,6 +604,42 @@ __global__ void __launch_bounds__(kWarpsN * 32, (min_ctas_n<D, Real>())) seidel_
             atomicExch(ws + kWsHeadMid, 0ull);
             atomicExch(ws + kWsHeadSmall, 0ull);
             atomicExch(ws + kWsDone, 0ull);
+        }
+    }
+}
+
+// The large-LP kernel: one warp per CTA, a stage of kStageNL slots per array and a key
+// bitmap for domains up to 4^7 = 16384 bits, in dynamic shared memory.
+constexpr int kStageNL = 8192;
+constexpr int kWordsNL = 512;
+constexpr int kWsDoneLargeN = 5;  // workspace word: large-LP CTAs that have finished
+
+template <int D, typename Real> constexpr size_t smem_bytes_nl() {
+    return sizeof(float) * (D + 1) * kStageNL + sizeof(Real) * kFrameReals<D> + sizeof(int) * D +
+           sizeof(unsigned) * kWordsNL + sizeof(int) * kWordsNL;
+}
+
+// LPs above the half stage: one warp per CTA; LPs above kStageNL - 2d constraints are
+// reported as too large.  Runs after seidel_nd_kernel on the same stream, with its own
+// queue head and done counter.
+template <typename Real, int D>
+__global__ void __launch_bounds__(32, 1) seidel_nd_large_kernel(const ParamsN P) {
+    extern __shared__ __align__(16) unsigned char smem_nl[];
+    float* stage = reinterpret_cast<float*>(smem_nl);
+    Real* fr = reinterpret_cast<Real*>(smem_nl + sizeof(float) * (D + 1) * kStageNL);
+    int* df = reinterpret_cast<int*>(fr + kFrameReals<D>);
+    unsigned* bm = reinterpret_cast<unsigned*>(df + D);
+    int* pre = reinterpret_cast<int*>(bm + kWordsNL);
+    const int lane = threadIdx.x;
+    unsigned long long* ws = P.ws;
+    warp_queue_n<Real, D, kStageNL, true>(P, ws + kWsHeadBig, kHalfN - 2 * D, 1ll << 62, stage, fr, df, bm, lane,
+                                          pre);
+    if (lane == 0) {
+        __threadfence();
+        const unsigned long long prev = atomicAdd(ws + kWsDoneLargeN, 1ull);
+        if (prev == static_cast<unsigned long long>(gridDim.x) - 1ull) {
+            atomicExch(ws + kWsHeadBig, 0ull);
+            atomicExch(ws + kWsDoneLargeN, 0ull);
         }
     }
 }
@@ -608,6 +659,7 @@ int launch_nd(const lp2d::ParamsN& p, int ctas_per_sm_cap, int64_t n_lp, cudaStr
     auto kernel = lp2d::seidel_nd_kernel<Real, D>;
     static std::mutex mu;
     static bool ready[64] = {};
+    static bool ready_large[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return report_error(LP2D_ERR_CUDA, "device query: %s", cudaGetErrorString(e));
@@ -634,6 +686,21 @@ int launch_nd(const lp2d::ParamsN& p, int ctas_per_sm_cap, int64_t n_lp, cudaStr
     kernel<<<static_cast<int>(grid), lp2d::kWarpsN * 32, bytes, s>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return report_error(LP2D_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    // LPs above the half stage: one CTA per SM, each a warp with a large stage
+    constexpr size_t lbytes = lp2d::smem_bytes_nl<D, Real>();
+    auto large = lp2d::seidel_nd_large_kernel<Real, D>;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!ready_large[dev]) {
+            e = cudaFuncSetAttribute(large, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(lbytes));
+            if (e != cudaSuccess)
+                return report_error(LP2D_ERR_CUDA, "large-LP shared memory opt-in: %s", cudaGetErrorString(e));
+            ready_large[dev] = true;
+        }
+    }
+    large<<<static_cast<int>(std::min<long long>(sms, n_lp)), 32, lbytes, s>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return report_error(LP2D_ERR_CUDA, "large-LP kernel launch: %s", cudaGetErrorString(e));
     return LP2D_OK;
 }
 

@@ -290,7 +290,7 @@ def solve_batch_host(ax, ay, b, offsets, obj, box, out_xy, out_status, options: 
 
 
 _3d_ready = False
-MAX_CONSTRAINTS_3D = 1018
+MAX_CONSTRAINTS_3D = 12282
 DEVERR_TOO_LARGE = 4
 
 
@@ -334,6 +334,12 @@ MAX_DIM = 5
 
 def max_constraints_nd(d: int) -> int:
     """LPND_MAX_CONSTRAINTS(d): the largest LP the d-dimensional solver stages."""
+    return 8192 - 2 * d
+
+
+def warp_stage_constraints_nd(d: int) -> int:
+    """The largest d-dimensional LP the main kernel stages (half of a CTA's stage); the
+    one-warp large-LP kernel takes the larger ones."""
     return 1024 - 2 * d
 
 

@@ -178,7 +178,7 @@ def test_nd_host_side_validation(lib):
     assert call(4, 3, a=(ctypes.c_void_p * 4)(al, al, None, al), p=ctypes.c_void_p(al)) == lib.ERR_INVALID_ARGUMENT
     assert "a[2]" in lib.last_error()
     assert call(4, 3, a=(ctypes.c_void_p * 4)(al, al, al, al + 2), p=ctypes.c_void_p(al)) == lib.ERR_INVALID_ARGUMENT
-    assert lib.max_constraints_nd(5) == 1014
+    assert lib.max_constraints_nd(5) == 8182 and lib.warp_stage_constraints_nd(5) == 1014
 
 
 def test_autotune_host_side_validation(lib):

@@ -96,7 +96,9 @@ def test_ragged3d_at_scale():
 
 def test_edge_cases_empty_tiny_bad_and_too_large():
     rng = np.random.default_rng(9)
-    sizes = np.array([0, 1, 2, 3, 6, 31, 32, 33, 505, 506, 507, 1018, 1019, 5000])
+    # the class boundaries (quarter and half stage), the large-LP kernel (1019 and up)
+    # and its cap (12282), and one LP above it
+    sizes = np.array([0, 1, 2, 3, 6, 31, 32, 33, 505, 506, 507, 1018, 1019, 2000, 5000, 12282, 12283])
     batch = workloads.sphere_batch(sizes, seed=7)
     got = gpu_solve3(batch, seed=1)
     ref = oracle3(batch, seed=1)
@@ -249,3 +251,19 @@ def test_degenerate_lifted_and_duplicate_constraints(prec):
     ref = oracle3(batch, seed=3)
     assert_parity3(batch, got, ref, TOL[prec])
     assert (ref["status"][::7] == oracle.INFEASIBLE).all()
+
+
+@pytest.mark.parametrize("prec", [lp2d.PREC_FP32, lp2d.PREC_FP64])
+def test_lps_beyond_the_warp_stage(prec):
+    # LPs of 1019 constraints and more run in the one-warp kernel with the large stage;
+    # mixed with small ones, 25 % infeasible.  FP64 also takes the oracle's exact path
+    # (violation counts).
+    sizes = np.array([1019, 2000, 5000, 40, 700, 1019, 2000, 5000, 3, 9000] * 3)
+    batch = workloads.sphere_batch(sizes, seed=21, infeasible_frac=0.25)
+    want = prec == lp2d.PREC_FP64
+    got = gpu_solve3(batch, seed=4, precision=prec, want=want)
+    ref = oracle3(batch, seed=4, want_nviol=want)
+    assert got["err"] == 0
+    assert_parity3(batch, got, ref, TOL[prec])
+    if want:
+        assert (got["nviol"] == ref["nviol"]).all()

@@ -107,7 +107,7 @@ def assert_primal_feasible(batch, got, slack=1e-4):
 @pytest.mark.parametrize("prec", [lp2d.PREC_FP32, lp2d.PREC_FP64])
 @pytest.mark.parametrize("d", [2, 3, 4, 5])
 def test_small_batches_match_the_oracle(d, prec):
-    cap = lp2d.max_constraints_nd(d)
+    cap = lp2d.warp_stage_constraints_nd(d)
     n_rag = 1000 if d < 5 else 400
     for sizes, seed in ((np.full(400, 40), 1), (workloads.loguniform_sizes(np.random.default_rng(d), n_rag, 1, cap - 1), 2)):
         batch = workloads.ball_batch(d, sizes, seed=seed + 10 * d, infeasible_frac=0.1)
@@ -116,7 +116,7 @@ def test_small_batches_match_the_oracle(d, prec):
 
 @pytest.mark.parametrize("d", [3, 4, 5])
 def test_fp64_violation_counts_and_defining_planes_match_the_oracle(d):
-    sizes = workloads.loguniform_sizes(np.random.default_rng(6 + d), 600, 1, lp2d.max_constraints_nd(d) - 1)
+    sizes = workloads.loguniform_sizes(np.random.default_rng(6 + d), 600, 1, lp2d.warp_stage_constraints_nd(d) - 1)
     batch = workloads.ball_batch(d, sizes, seed=4, infeasible_frac=0.1)
     got = gpu_solve_nd(batch, seed=5, precision=lp2d.PREC_FP64, want=True)
     ref = oracle_nd(batch, seed=5, want_def=True, want_nviol=True)
@@ -149,8 +149,11 @@ def test_ragged_at_scale(d):
 def test_edge_cases_empty_tiny_bad_and_too_large(d):
     cap = lp2d.max_constraints_nd(d)
     small = 512 - 2 * d
-    sizes = np.array([0, 1, 2, d, 2 * d - 1, 2 * d, 31, 32, 33, small - 1, small, small + 1, cap - 1, cap, cap + 1,
-                      5000])
+    half = lp2d.warp_stage_constraints_nd(d)
+    # the quarter- and half-stage boundaries, the large-LP kernel up to its cap, and
+    # one LP above the cap
+    sizes = np.array([0, 1, 2, d, 2 * d - 1, 2 * d, 31, 32, 33, small - 1, small, small + 1, half - 1, half, half + 1,
+                      5000, cap - 1, cap, cap + 1])
     batch = workloads.ball_batch(d, sizes, seed=7)
     got = gpu_solve_nd(batch, seed=1)
     keep = sizes <= cap
@@ -246,3 +249,20 @@ def test_duplicate_and_zero_normal_constraints_match_the_oracle(d):
         assert_parity(batch["obj"], got, ref, TOL[prec])
     # 0.x <= -1 excludes everything: every seventh LP is infeasible
     assert (ref["status"][::7] == oracle.INFEASIBLE).all()
+
+
+@pytest.mark.parametrize("prec", [lp2d.PREC_FP32, lp2d.PREC_FP64])
+@pytest.mark.parametrize("d", [3, 4, 5])
+def test_lps_beyond_the_warp_stage(d, prec):
+    # LPs above half of a CTA's stage run in the one-warp large-LP kernel, mixed with
+    # small ones, 25 % infeasible; FP64 also follows the oracle's exact path
+    half = lp2d.warp_stage_constraints_nd(d)
+    sizes = np.array([half + 1, 2000, 5000, 40, 300, half + 1, 2000, 5000, 7, 3000] * 2)
+    batch = workloads.ball_batch(d, sizes, seed=20 + d, infeasible_frac=0.25)
+    want = prec == lp2d.PREC_FP64
+    got = gpu_solve_nd(batch, seed=2, precision=prec, want=want)
+    ref = oracle_nd(batch, seed=2, want_nviol=want)
+    assert got["err"] == 0
+    assert_parity(batch["obj"], got, ref, TOL[prec])
+    if want:
+        assert (got["nviol"] == ref["nviol"]).all()
