@@ -71,9 +71,10 @@ def dist_env():
 
 # the sources the FP32 persistent kernel is compiled from (the entry-point file and the
 # other kernels do not change its code)
-KERNEL_SOURCES = ("lp2d_device.cuh", "lp2d_internal.h", "lp2d_persistent.cu", "lp2d_solve.cuh", "lp2d_staged.cuh")
-KERNEL_SOURCES_3D = ("lp2d_device.cuh", "lp2d_internal.h", "lp2d_staged.cuh", "lp3d.cu")
-KERNEL_SOURCES_ND = ("lp2d_device.cuh", "lp2d_internal.h", "lp2d_staged.cuh", "lpnd.cu")
+KERNEL_SOURCES = ("lp2d_device.cuh", "lp2d_internal.h", "lp2d_persistent.cu", "lp2d_solve.cuh", "lp2d_staged.cuh",
+                  "lp2d_warp.cuh")
+KERNEL_SOURCES_3D = ("lp2d_device.cuh", "lp2d_internal.h", "lp2d_staged.cuh", "lp3d.cu", "lp_stage_big.cuh")
+KERNEL_SOURCES_ND = ("lp2d_device.cuh", "lp2d_internal.h", "lp2d_staged.cuh", "lpnd.cu", "lp_stage_big.cuh")
 
 
 def kernel_source_hash(files=KERNEL_SOURCES) -> str:
@@ -84,18 +85,45 @@ def kernel_source_hash(files=KERNEL_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, files=KERNEL_SOURCES):
-    """DRAM bytes per launch recorded by an ncu capture of the current kernel source,
-    from the summaries under profiles/ (None when no capture matches the source)."""
+def profiled_metric(workload: str, files=KERNEL_SOURCES, key="traffic_bytes_per_launch"):
+    """A per-launch figure (DRAM bytes, warp-instructions) recorded by an ncu capture of
+    the current kernel source, from the summaries under profiles/ (None when no
+    capture matches the source)."""
     src = kernel_source_hash(files)
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         text = open(path).read()
         m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", text)
         m_wl = re.search(r"workload:\s*(\S+)", text)
-        m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
+        m_tr = re.search(key + r":\s*([0-9]+)", text)
         if m_hash and m_tr and m_wl and m_hash.group(1) == src and m_wl.group(1) == workload:
             return int(m_tr.group(1))
     return None
+
+
+def profiled_traffic(workload: str, files=KERNEL_SOURCES):
+    return profiled_metric(workload, files, "traffic_bytes_per_launch")
+
+
+def sm_count(dev) -> int:
+    import torch
+
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
+
+
+def issue_roofline(workload: str, files, ms: float, sms: int, hbm: dict):
+    """Ceiling of a compute-bound kernel: its warp-instructions per solve (ncu, from the
+    summary of the current source) against the issue rate of the GPU, one instruction
+    per scheduler per cycle (SMs x 4 schedulers x the maximum SM clock)."""
+    inst = profiled_metric(workload, files, "inst_executed_per_solve")
+    mhz = 2070.0
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        mhz = float(json.load(open(path)).get("sm_max_mhz", mhz))
+    peak = sms * 4 * mhz * 1e6
+    achieved = inst / (ms * 1e-3) if inst is not None else None
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp-instructions/s",
+            "frac": achieved / peak if achieved is not None else None, "inst_per_solve": inst,
+            "peak_kind": f"{sms} SMs x 4 schedulers x {mhz:.0f} MHz", "hbm": hbm}
 
 
 def measured_peaks():
@@ -369,11 +397,12 @@ def measure_lp3d(args, dev, stream, peak, world, rank=0):
     line = {
         "workload": "ragged3d_65536_logu8_1017", "n_lp": n3, "n_constraints": int(b3["offsets"][-1]),
         "value": n3 * world / (ms3 * 1e-3), "unit": UNIT, "ms_per_step": ms3, "status_counts": status3,
-        "roofline": {"bound": "hbm", "achieved": algo3 / (ms3 * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
-                     "frac": algo3 / (ms3 * 1e-3) / 1e9 / peak,
-                     "algorithmic_bytes": algo3, "per_unit": "16 B per constraint + 36 B per LP",
-                     "traffic": profiled_traffic("ragged3d_65536_logu8_1017", KERNEL_SOURCES_3D)},
-        "kernel": "seidel3_kernel<float>", "dtype": "f32",
+        "roofline": issue_roofline("ragged3d_65536_logu8_1017", KERNEL_SOURCES_3D, ms3, sm_count(dev), {
+            "achieved": algo3 / (ms3 * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": algo3 / (ms3 * 1e-3) / 1e9 / peak, "algorithmic_bytes": algo3,
+            "per_unit": "16 B per constraint + 36 B per LP",
+            "traffic": profiled_traffic("ragged3d_65536_logu8_1017", KERNEL_SOURCES_3D)}),
+        "kernel": "seidel3_kernel<float> + seidel3_large_kernel<float>", "dtype": "f32",
         "least_violation": {"workload": "ragged_131072_logu8_1017 (its infeasible LPs)", "infeasible_lps": n_inf,
                             "ms_per_step": ms_lv, "value": n_inf / (ms_lv * 1e-3), "unit": "infeasible LPs/s",
                             "kernel": "seidel3_kernel<float> (least-violation mode)"},
@@ -435,11 +464,13 @@ def measure_lpnd(args, dev, stream, peak, world, rank=0, dims=(4, 5)):
             "workload": f"ragged{d}d_65536_logu8_{1023 - 2 * d}", "n_lp": n, "n_constraints": int(bd["offsets"][-1]),
             "value": n * world / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
             "status_counts": np.bincount(st.cpu().numpy(), minlength=4).tolist(),
-            "roofline": {"bound": "hbm", "achieved": algo / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+            "roofline": issue_roofline(f"ragged{d}d_65536_logu8_{1023 - 2 * d}", KERNEL_SOURCES_ND, ms,
+                                       sm_count(dev), {
+                         "achieved": algo / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": algo / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes": algo,
                          "per_unit": f"{4 * d + 4} B per constraint + {8 * d + 12} B per LP",
-                         "traffic": profiled_traffic(f"ragged{d}d_65536_logu8_{1023 - 2 * d}", KERNEL_SOURCES_ND)},
-            "kernel": f"seidel_nd_kernel<float, {d}>", "dtype": "f32",
+                         "traffic": profiled_traffic(f"ragged{d}d_65536_logu8_{1023 - 2 * d}", KERNEL_SOURCES_ND)}),
+            "kernel": f"seidel_nd_kernel<float, {d}> + seidel_nd_large_kernel<float, {d}>", "dtype": "f32",
         }
         if not args.no_cpu_baseline and world == 1:
             import oracle

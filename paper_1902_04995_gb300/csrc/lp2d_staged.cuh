@@ -216,15 +216,36 @@ __device__ __forceinline__ void wu_range(const float* __restrict__ sX, const flo
     if constexpr (kFlag) *np = near;
 }
 
-// Warp-wide reduction of the 1-D LP state; every lane gets the result.
+// Warp-wide float minimum and maximum (redux.sync on 32-bit floats).
+__device__ __forceinline__ float redux_min_f32(float v) {
+    float r;
+    asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;\n" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float redux_max_f32(float v) {
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;\n" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// Warp-wide reduction of the 1-D LP state; every lane gets the result: the minimum
+// right bound with its lowest slot, the maximum left bound.  FP32 reduces the floats
+// directly (redux.sync); FP64 reduces order-preserving 64-bit keys by shuffles.
 template <typename Real>
 __device__ __forceinline__ void warp_reduce_1dlp(Real& thi, int& phi, Real& tlo) {
-    using KT = KeyOf<Real>;
-    typename KT::type khi = KT::key(thi), klo = KT::key(tlo);
-    warp_min_pair(khi, phi);
-    klo = warp_max_key(klo);
-    thi = KT::val(khi);
-    tlo = KT::val(klo);
+    if constexpr (sizeof(Real) == 4) {
+        const float m = redux_min_f32(thi);
+        phi = __reduce_min_sync(kFull, thi == m ? phi : kNoPos);
+        thi = m;
+        tlo = redux_max_f32(tlo);
+    } else {
+        using KT = KeyOf<Real>;
+        typename KT::type khi = KT::key(thi), klo = KT::key(tlo);
+        warp_min_pair(khi, phi);
+        klo = warp_max_key(klo);
+        thi = KT::val(khi);
+        tlo = KT::val(klo);
+    }
 }
 
 // Shared-memory protocol between the driving warp and its helpers.

@@ -42,32 +42,12 @@ __device__ __forceinline__ void prefetch_l2(const float* p, int64_t n) {
     }
 }
 
-__device__ __forceinline__ float redux_min_f32(float v) {
-    float r;
-    asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;\n" : "=f"(r) : "f"(v));
-    return r;
-}
-__device__ __forceinline__ float redux_max_f32(float v) {
-    float r;
-    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;\n" : "=f"(r) : "f"(v));
-    return r;
-}
-
 // Warp-wide reduction of a 1-D LP: (min right bound, its lowest slot), max left bound.
 // FP32: the float min/max of redux.sync; FP64: butterfly shuffles on order-preserving
 // 64-bit keys.  Every lane gets the result.
-__device__ __forceinline__ void reduce_1dlp(float& thi, int& phi, float& tlo) {
-    const float m = redux_min_f32(thi);
-    phi = __reduce_min_sync(kFull, thi == m ? phi : kNoPos);
-    thi = m;
-    tlo = redux_max_f32(tlo);
-}
-__device__ __forceinline__ void reduce_1dlp(double& thi, int& phi, double& tlo) {
-    long long khi = double_key(thi), klo = double_key(tlo);
-    warp_min_pair(khi, phi);
-    klo = warp_max_key(klo);
-    thi = key_double(khi);
-    tlo = key_double(klo);
+template <typename Real>
+__device__ __forceinline__ void reduce_1dlp(Real& thi, int& phi, Real& tlo) {
+    warp_reduce_1dlp<Real>(thi, phi, tlo);
 }
 
 // x * 0 is NaN exactly when x is NaN or infinite: folds the finiteness of a
