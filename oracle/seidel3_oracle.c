@@ -30,6 +30,10 @@
  *   - 1-D LPs follow the 2-D solver's rules: strict comparisons (the earliest
  *     position wins ties, box first), den == 0 excludes the line iff num < 0, the
  *     left end is taken when the objective is perpendicular to the line.
+ * Parity unpinned for two of these readings: the choice of u (the axis e_j) and the
+ * first-pair rule of the start decide only degenerate inputs (ties of measure zero on
+ * generic data), and no pin tells them from the alternatives.  Everything else here
+ * is pinned by the tests of the 3-D oracle.
  */
 #include <math.h>
 #include <stdint.h>
