@@ -71,8 +71,8 @@ def dist_env():
 
 # the sources the FP32 persistent kernel is compiled from (the entry-point file and the
 # other kernels do not change its code)
-KERNEL_SOURCES = ("lp2d_device.cuh", "lp2d_internal.h", "lp2d_persistent.cu", "lp2d_solve.cuh", "lp2d_staged.cuh",
-                  "lp2d_warp.cuh")
+KERNEL_SOURCES = ("lp2d_device.cuh", "lp2d_internal.h", "lp2d_lane.cuh", "lp2d_persistent.cu", "lp2d_solve.cuh",
+                  "lp2d_staged.cuh", "lp2d_warp.cuh")
 KERNEL_SOURCES_3D = ("lp2d_device.cuh", "lp2d_internal.h", "lp2d_staged.cuh", "lp3d.cu", "lp_stage_big.cuh")
 KERNEL_SOURCES_ND = ("lp2d_device.cuh", "lp2d_internal.h", "lp2d_staged.cuh", "lpnd.cu", "lp_stage_big.cuh")
 
@@ -637,9 +637,9 @@ def run_ours(args):
         tune_ms = solver.autotune(t["ax"], t["ay"], t["b"], t["offsets"], obj, box, reps=2, stream=stream)
         o = solver.options
         tune = {"ctas_per_sm": o.ctas_per_sm, "chunk_big": o.chunk_big, "chunk_small": o.chunk_small,
-                "team_min_slots": o.team_min_slots, "ms_per_solve": tune_ms,
+                "team_min_slots": o.team_min_slots, "lane_max_m": o.lane_max_m, "ms_per_solve": tune_ms,
                 "grid": "ctas_per_sm {occ, occ-1} x chunk_big {1,2,4} x chunk_small {1,2,4,8} x "
-                        "team_min_slots {512,1024,4096}"}
+                        "team_min_slots {512,1024,4096} x lane_max_m {-1,8,16}"}
     with torch.cuda.stream(stream):
         for _ in range(3):
             solver(t["ax"], t["ay"], t["b"], t["offsets"], obj, box)

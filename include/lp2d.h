@@ -119,6 +119,11 @@ typedef struct {
     int32_t l2_prefetch;    /**< persistent schedule: 1 = bulk-prefetch the constraints of every
                                  LP a CTA or warp takes from the queue into L2; 0 (default) or
                                  -1 = no prefetch */
+    int32_t lane_max_m;     /**< persistent schedule, LP2D_PREC_FP32: an LP of at most this many
+                                 constraints is solved by a single thread, 32 LPs per warp, from
+                                 shared memory (threads per LP 1 instead of 32; the results are
+                                 bit-identical); 1..16; 0 = default 16; -1 = every LP gets a
+                                 whole warp.  Ignored by the other precisions and schedules. */
 } lp2d_options;
 
 /** Fill *opt with the defaults listed above. */
@@ -247,10 +252,11 @@ int lp2d_visit_order(uint64_t seed_l, int64_t m, int64_t* out, lp2d_stream_t str
  * Autotune the persistent schedule for a batch: solve it with each candidate of a
  * small grid -- ctas_per_sm in {the occupancy limit, one less}, chunk_big in
  * {1, 2, 4}, chunk_small in {1, 2, 4, 8}, team_min_slots (threads per 1-D LP of a
- * CTA-staged LP: 128 from 512 or 1024 slots on, or always 32) in {512, 1024, 4096} --
+ * CTA-staged LP: 128 from 512 or 1024 slots on, or always 32) in {512, 1024, 4096},
+ * lane_max_m (threads per LP: 1 up to this size, 32 above) in {-1, 8, 16} --
  * timing `reps` solves per candidate with CUDA events on `stream` after one warm-up
  * solve, and write the fastest into opt->ctas_per_sm / chunk_big / chunk_small /
- * team_min_slots (the other fields of *opt are the base
+ * team_min_slots / lane_max_m (the other fields of *opt are the base
  * options of every trial; out_nviol / out_def are not written).  The tuned fields
  * change only the speed: results are the same for every setting.  The arguments
  * are those of lp2d_solve_batch_ex; out_xy / out_status hold the last trial's

@@ -98,6 +98,7 @@ void lp2d_default_options(lp2d_options* opt) {
     opt->out_def = nullptr;
     opt->team_min_slots = 0;
     opt->l2_prefetch = 0;
+    opt->lane_max_m = 0;
 }
 
 size_t lp2d_workspace_bytes(int64_t n_lp, const lp2d_options* opt) {
@@ -134,6 +135,9 @@ int lp2d_solve_batch_ex(const float* ax, const float* ay, const float* b, const 
                     opt.team_min_slots);
     if (opt.l2_prefetch < -1 || opt.l2_prefetch > 1)
         return fail(LP2D_ERR_INVALID_ARGUMENT, "l2_prefetch = %d is not -1, 0 or 1", opt.l2_prefetch);
+    if (opt.lane_max_m < -1 || opt.lane_max_m > lp2d::kCapLane)
+        return fail(LP2D_ERR_INVALID_ARGUMENT, "lane_max_m = %d outside -1..%d (0 = default, -1 = none)",
+                    opt.lane_max_m, lp2d::kCapLane);
     if (!(opt.eps >= 0.0f) || !finite(opt.eps) || !(opt.near_parallel_tau >= 0.0f) || !finite(opt.near_parallel_tau))
         return fail(LP2D_ERR_INVALID_ARGUMENT, "eps / near_parallel_tau must be finite and >= 0");
     if (!finite(box.xmin) || !finite(box.xmax) || !finite(box.ymin) || !finite(box.ymax) ||
@@ -189,6 +193,7 @@ int lp2d_solve_batch_ex(const float* ax, const float* ay, const float* b, const 
     p.check_finite = opt.check_finite ? 1 : 0;
     p.team_min = opt.team_min_slots > 0 ? opt.team_min_slots : lp2d::kDefaultTeamMin;
     p.prefetch = opt.l2_prefetch > 0 ? 1 : 0;
+    p.lane_max_m = opt.lane_max_m > 0 ? opt.lane_max_m : (opt.lane_max_m == 0 ? lp2d::kDefaultLaneMax : 0);
 
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const bool fp64 = opt.precision == LP2D_PREC_FP64;
@@ -274,17 +279,20 @@ int lp2d_autotune(const float* ax, const float* ay, const float* b, const int64_
     // threads per 1-D LP of a CTA-staged LP: from 512 (or 1024) earlier constraints on
     // the CTA's 128 threads, or always the driving warp's 32 (4096 exceeds every stage)
     const int teams[3] = {512, 1024, 4096};
+    // threads per LP: 1 (32 LPs per warp) up to this size, 32 above; -1: always 32
+    const int lanes[3] = {-1, 8, lp2d::kCapLane};
     float best = -1.0f;
     lp2d_options winner = base;
     for (int ci = 0; ci < 2 && rc == LP2D_OK; ++ci) {
         if (ci == 1 && ctas[1] == ctas[0]) break;
         for (int bi = 0; bi < 3 && rc == LP2D_OK; ++bi) {
-            for (int si = 0; si < 4 * 3 && rc == LP2D_OK; ++si) {
+            for (int si = 0; si < 4 * 3 * 3 && rc == LP2D_OK; ++si) {
                 lp2d_options o = base;
                 o.ctas_per_sm = ctas[ci];
                 o.chunk_big = bigs[bi];
                 o.chunk_small = smalls[si % 4];
-                o.team_min_slots = teams[si / 4];
+                o.team_min_slots = teams[(si / 4) % 3];
+                o.lane_max_m = lanes[si / 12];
                 rc = lp2d_solve_batch_ex(ax, ay, b, offsets, n_lp, obj_xy, box, out_xy, out_status, &o, workspace,
                                          workspace_bytes, stream);  // warm-up
                 if (rc != LP2D_OK) break;
@@ -314,6 +322,7 @@ int lp2d_autotune(const float* ax, const float* ay, const float* b, const int64_
     opt->chunk_big = winner.chunk_big;
     opt->chunk_small = winner.chunk_small;
     opt->team_min_slots = winner.team_min_slots;
+    opt->lane_max_m = winner.lane_max_m;
     if (out_best_ms) *out_best_ms = best;
     return ok();
 }

@@ -28,6 +28,7 @@ constexpr int kWsHeadSmall = 1;  // next LP index for single warps
 constexpr int kWsDone = 2;       // CTAs that have finished
 constexpr int kWsError = 3;      // device error word
 constexpr int kWsHeadMid = 4;    // next LP index for warps with half a CTA stage
+constexpr int kWsHeadTiny = 6;   // next LP index for single lanes
 constexpr int kWsWords = 32;     // 256 bytes
 
 struct Params {
@@ -52,6 +53,7 @@ struct Params {
     int check_finite;
     int team_min;   // 1-D LPs over at least this many stage slots get the CTA's helper warps
     int prefetch;   // non-zero: bulk-prefetch each grabbed LP's constraints into L2
+    int lane_max_m;  // FP32: LPs of at most this many constraints go to single lanes (0: none)
 };
 
 // ------------------------------------------------------------------ visit order

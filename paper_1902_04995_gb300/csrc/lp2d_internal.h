@@ -15,6 +15,8 @@ constexpr int kCapSmall = 512;        // largest LP one warp stages in a quarter
 constexpr int kCapMid = 1024;         // largest LP one warp stages in half of the stage (its keys fit 32 words)
 constexpr int kCapBig = 2060;         // largest LP the CTA stages (the box and 2060 constraints)
 constexpr int kDefaultTeamMin = 1024; // 1-D LPs over at least this many slots get the helper warps
+constexpr int kCapLane = 16;          // largest LP one lane solves alone (32 per warp stage)
+constexpr int kDefaultLaneMax = 16;   // default largest LP solved by one lane (FP32)
 constexpr int kMaxChunk = 32;         // LP indices per queue grab, at most
 constexpr int kMaxChunkSmall = 16;    // largest target of LPs per warp grab
 constexpr int kDefaultChunkBig = 1;   // target large LPs per CTA grab

@@ -12,11 +12,14 @@
 //            warp for warps 0 and 1, each with half of the stage (their 1-D LPs are
 //            too short for helpers, so two drivers share a CTA's stage);
 //   phase 3: LPs with at most kCapSmall constraints, one per warp, each warp with a
-//            quarter of the stage.
+//            quarter of the stage;
+//   phase 4 (FP32): LPs with at most P.lane_max_m (<= kCapLane) constraints, one per
+//            lane, 32 per warp (lp2d_lane.cuh); phase 3 then leaves them out.
 // Large LPs therefore start first and small ones fill the tail.  The last CTA to
 // finish resets the queue heads, so the workspace is ready for the next launch on
 // the same stream without a memset.
 #include "lp2d_internal.h"
+#include "lp2d_lane.cuh"
 #include "lp2d_solve.cuh"
 #include "lp2d_warp.cuh"
 
@@ -38,6 +41,7 @@ constexpr int kKeysBig = (kCapBig + 127) / 128;
 constexpr int kRowsBig = 2;
 constexpr int kRowsMid = 1;
 constexpr int kRowsSmall = 1;
+static_assert(32 * kLaneCap <= kWarpSlots && kCapLane <= kLaneCap, "32 single-lane LPs fill a warp's stage");
 
 // The FP32 iterations have their own driver (Rows rows of 32 positions per step); the
 // other precisions share drive_lp2.
@@ -116,6 +120,8 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
     const int warp = tid >> 5;
     const int lane = tid & 31;
     unsigned phase = 0;
+    // the largest LP solved by a single lane (FP32 only; 0: none)
+    const int tiny = (sizeof(Real) == 4 && !kMixed) ? P.lane_max_m : 0;
     unsigned long long* ws = P.ws;
 
     // ---- phase 1: large LPs, one CTA each (grab spans adapt as in next_span)
@@ -217,8 +223,9 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
         float cx_l, cy_l;
         const long long start = warp_grab(P, ws + kWsHeadSmall, span, lane, off_l, mm_l, cx_l, cy_l);
         if (start < 0 || start >= P.n_lp) break;
-        // negative sizes (bad offsets) are reported here
-        unsigned todo = __ballot_sync(kFull, lane < span && start + lane < P.n_lp && mm_l <= kCapSmall);
+        // negative sizes (bad offsets) are reported here; LPs for single lanes are not
+        unsigned todo = __ballot_sync(kFull, lane < span && start + lane < P.n_lp && mm_l <= kCapSmall &&
+                                                 !(tiny > 0 && mm_l >= 0 && mm_l <= tiny));
         span = next_span(span, __popc(todo), P.chunk_small);
         prefetch_grab(P, todo, off_l, mm_l, lane);
         while (todo != 0u) {
@@ -243,6 +250,59 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
         }
     }
 
+    // ---- phase 4 (FP32): LPs of at most `tiny` constraints, one lane each, 32 per warp,
+    // in the warp's part of the stage (position p of lane l in slot 32 p + l)
+    if (tiny > 0) {
+        // pending LPs: lane i < np holds the i-th (index, first offset, size, objective);
+        // a grab spans only the lanes still free, so the list never overflows
+        long long p_lp = 0, p_off = 0;
+        int p_m = 0;
+        float p_cx = 0.0f, p_cy = 0.0f;
+        int np = 0;
+        bool more = true;
+        for (;;) {
+            while (more && np < 32) {
+                const int span = 32 - np;
+                long long off_l, mm_l;
+                float cx_l, cy_l;
+                const long long start = warp_grab(P, ws + kWsHeadTiny, span, lane, off_l, mm_l, cx_l, cy_l);
+                if (start < 0 || start >= P.n_lp) {
+                    more = false;
+                    break;
+                }
+                const unsigned found =
+                    __ballot_sync(kFull, lane < span && start + lane < P.n_lp && mm_l >= 0 && mm_l <= tiny);
+                const int cnt = __popc(found);
+                // lanes np .. np + cnt - 1 take the found LPs in index order
+                const int t = lane - np;
+                const bool take = t >= 0 && t < cnt;
+                const int src = take ? nth_set_bit(found, t) : lane;
+                const long long o = __shfl_sync(kFull, off_l, src);
+                const long long n = __shfl_sync(kFull, mm_l, src);
+                const float ocx = __shfl_sync(kFull, cx_l, src), ocy = __shfl_sync(kFull, cy_l, src);
+                if (take) {
+                    p_lp = start + src;
+                    p_off = o;
+                    p_m = static_cast<int>(n);
+                    p_cx = ocx;
+                    p_cy = ocy;
+                }
+                np += cnt;
+            }
+            if (np == 0) break;
+            const bool valid = lane < np;
+            const int m = valid ? p_m : 0;
+            VisitOrder vo;
+            vo.init(P.seed + static_cast<uint64_t>(p_lp), static_cast<uint32_t>(m));
+            const uint64_t ord = stage_lane(vo, m, P.ax + p_off, P.ay + p_off, P.b + p_off, wA, wB, lane);
+            cp_async_wait_all();
+            __syncwarp();
+            solve_lane_f32(P, p_lp, valid, m, p_cx, p_cy, ord, wA, wB, lane);
+            __syncwarp();  // all lanes are done with the stage before it is overwritten
+            np = 0;
+        }
+    }
+
     // ---- the last CTA out resets the queue heads for the next launch
     __syncthreads();
     if (tid == 0) {
@@ -252,6 +312,7 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
             atomicExch(ws + kWsHeadBig, 0ull);
             atomicExch(ws + kWsHeadSmall, 0ull);
             atomicExch(ws + kWsHeadMid, 0ull);
+            atomicExch(ws + kWsHeadTiny, 0ull);
             atomicExch(ws + kWsDone, 0ull);
         }
     }

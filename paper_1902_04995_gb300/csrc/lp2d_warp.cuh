@@ -608,7 +608,7 @@ __device__ void drive_f32(const Params& P, int64_t lp, int m, float cx, float cy
         const float lx = __shfl_sync(kFull, rowa.x, src);
         const float ly = __shfl_sync(kFull, rowa.y, src);
         const float lb = __shfl_sync(kFull, rowb, src);
-        const float nrm2 = lx * lx + ly * ly;
+        const float nrm2 = fmaf(lx, lx, ly * ly);  // the lane-group driver's forms
         if (!(nrm2 != 0.0f)) {  // 0.x <= lb < 0 (NaN data also stops here)
             status = kInfeasible;
             break;
@@ -617,7 +617,7 @@ __device__ void drive_f32(const Params& P, int64_t lp, int m, float cx, float cy
         const float p0x = lx * sc0, p0y = ly * sc0;  // foot of l
         // direction of l, oriented so that the objective's end is the right end; when
         // c.u == 0 the left end of u = (-ly, lx) is taken
-        const float cu = cx * (-ly) + cy * lx;
+        const float cu = fmaf(cx, -ly, cy * lx);
         const float ux = (cu > 0.0f) ? -ly : ly;
         const float uy = (cu > 0.0f) ? lx : -lx;
         float thi = real_inf<float>(), tlo = -real_inf<float>();
@@ -673,8 +673,8 @@ __device__ void drive_f32(const Params& P, int64_t lp, int m, float cx, float cy
             status = kInfeasible;
             break;
         }
-        vx = p0x + thi * ux;
-        vy = p0y + thi * uy;
+        vx = fmaf(thi, ux, p0x);
+        vy = fmaf(thi, uy, p0y);
         ex = eps * fabsf(vx);
         ey = eps * fabsf(vy);
         d0 = fslot;

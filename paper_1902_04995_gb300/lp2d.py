@@ -43,6 +43,7 @@ class Options(ctypes.Structure):
         ("out_def", ctypes.c_void_p),
         ("team_min_slots", ctypes.c_int32),
         ("l2_prefetch", ctypes.c_int32),
+        ("lane_max_m", ctypes.c_int32),
     ]
 
 

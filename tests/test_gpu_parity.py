@@ -195,7 +195,8 @@ def test_results_identical_across_tuning():
     base = gpu_solve(batch, seed=2)
     for tune in ({"ctas_per_sm": 1}, {"ctas_per_sm": 3, "chunk_big": 1, "chunk_small": 1},
                  {"chunk_big": 16, "chunk_small": 8}, {"team_min_slots": 64}, {"team_min_slots": 4096},
-                 {"l2_prefetch": -1, "team_min_slots": 300}):
+                 {"l2_prefetch": -1, "team_min_slots": 300}, {"lane_max_m": -1}, {"lane_max_m": 1},
+                 {"lane_max_m": 16, "chunk_small": 1}):
         got = gpu_solve(batch, seed=2, **tune)
         assert (got["status"] == base["status"]).all()
         assert np.array_equal(got["xy"], base["xy"], equal_nan=True), tune
@@ -210,10 +211,37 @@ def test_batches_of_one_size_class(lo, hi, n_lp):
     batch = workloads.disk_batch(sizes, seed=lo + hi, infeasible_frac=0.1)
     base = gpu_solve(batch, seed=4)
     assert_parity(batch, base, oracle_solve(batch, seed=4), TOL[lp2d.PREC_FP32])
-    for tune in ({"chunk_big": 32, "chunk_small": 16}, {"chunk_big": 1, "chunk_small": 1, "ctas_per_sm": 2}):
+    for tune in ({"chunk_big": 32, "chunk_small": 16}, {"chunk_big": 1, "chunk_small": 1, "ctas_per_sm": 2},
+                 {"lane_max_m": -1}, {"lane_max_m": 16}):
         got = gpu_solve(batch, seed=4, **tune)
         assert (got["status"] == base["status"]).all(), tune
         assert np.array_equal(got["xy"], base["xy"], equal_nan=True), tune
+
+
+@pytest.mark.parametrize("lane_max_m", [8, 16])
+def test_single_lane_lps_match_whole_warps(lane_max_m):
+    # LPs of 0..16 constraints (a tenth infeasible, a few with NaN data) among larger
+    # ones, solved one per lane and one per warp: the same statuses, vertices, violation
+    # counts and defining constraints, bit for bit, and the oracle's results.
+    rng = np.random.default_rng(lane_max_m)
+    sizes = np.concatenate([np.arange(0, 17), rng.integers(0, lane_max_m + 1, 20000), rng.integers(1, 200, 3000)])
+    rng.shuffle(sizes)
+    batch = workloads.disk_batch(sizes, seed=77, infeasible_frac=0.1)
+    starts = batch["offsets"][:-1][sizes > 3]
+    batch["ax"][starts[::501] + 1] = np.nan
+    lanes = gpu_solve(batch, seed=8, want=True, lane_max_m=lane_max_m)
+    whole = gpu_solve(batch, seed=8, want=True, lane_max_m=-1)
+    assert (lanes["status"] == whole["status"]).all()
+    assert np.array_equal(lanes["xy"], whole["xy"], equal_nan=True)
+    assert (lanes["nviol"] == whole["nviol"]).all()
+    ok = (whole["status"] == oracle.OPTIMAL) | (whole["status"] == oracle.BOX_BOUNDED)
+    assert (lanes["def"][ok] == whole["def"][ok]).all()
+    ref = oracle_solve(batch, seed=8, want_def=True)
+    assert (ref["status"] == oracle.BAD_INPUT).sum() == starts[::501].size
+    assert_parity(batch, lanes, ref, TOL[lp2d.PREC_FP32])
+    solved = ref["status"] != oracle.INFEASIBLE
+    same = (np.sort(lanes["def"][solved & ok], 1) == np.sort(ref["def"][solved & ok][:, :2], 1)).all(1)
+    assert same.mean() >= 0.999
 
 
 def test_autotune_picks_a_grid_point_and_keeps_the_results():
@@ -226,6 +254,7 @@ def test_autotune_picks_a_grid_point_and_keeps_the_results():
     assert ms > 0.0
     assert o.chunk_big in (1, 2, 4) and o.chunk_small in (1, 2, 4, 8) and o.ctas_per_sm >= 1
     assert o.team_min_slots in (512, 1024, 4096)
+    assert o.lane_max_m in (-1, 8, 16)
     solver(t["ax"], t["ay"], t["b"], t["offsets"], t["obj"].reshape(-1), batch["box"])
     torch.cuda.synchronize()
     assert (solver.out_status.cpu().numpy() == base["status"]).all()
