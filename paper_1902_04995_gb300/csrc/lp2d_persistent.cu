@@ -64,14 +64,19 @@ __device__ __forceinline__ void write_bad(const Params& P, int64_t lp) {
 }
 
 // Span of the next queue grab: a grab that held none of the caller's LPs doubles it
-// (up to 32), one that held more than `target` of them halves it (down to 1).  A
+// (up to `cap`), one that held more than `target` of them halves it (down to 1).  A
 // class that is rare in the batch thus costs few queue operations, and a dense one
 // keeps grabs small enough to balance the load across the grid.
-__device__ __forceinline__ int next_span(int span, int found, int target) {
-    if (found == 0) return min(2 * span, 32);
+__device__ __forceinline__ int next_span(int span, int found, int target, int cap = 32) {
+    if (found == 0) return min(2 * span, cap);
     if (found > target) return max(span >> 1, 1);
     return span;
 }
+
+// Largest span of phases 1 and 2, whose classes fill about an eighth of the LP indices
+// each: a grab of 32 can hold several of their LPs, which one CTA or warp then solves
+// one after another while the others run out of work at the end of the phase.
+constexpr int kSpanCapSparse = 16;
 
 // A warp's next grab from the queue at *head: `span` LP indices starting at the
 // returned index; lane l < span gets the first offset, the size and the objective of
@@ -172,7 +177,7 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
                 team_helper2<Real, kMixed>(sA, sB, &job, tid);
             __syncthreads();
         }
-        big_span = next_span(big_span, found, P.chunk_big);
+        big_span = next_span(big_span, found, P.chunk_big, kSpanCapSparse);
     }
 
     // ---- phase 2: mid-size LPs, one warp each for warps 0 and 1 (half a stage each)
@@ -189,7 +194,7 @@ __device__ __forceinline__ void persistent_body(const Params& P) {
             const long long start = warp_grab(P, ws + kWsHeadMid, span, lane, off_l, mm_l, cx_l, cy_l);
             if (start < 0 || start >= P.n_lp) break;
             unsigned todo = __ballot_sync(kFull, lane < span && mm_l > kCapSmall && mm_l <= kCapMid);
-            span = next_span(span, __popc(todo), P.chunk_small);
+            span = next_span(span, __popc(todo), P.chunk_small, kSpanCapSparse);
             prefetch_grab(P, todo, off_l, mm_l, lane);
             while (todo != 0u) {
                 const int i = __ffs(todo) - 1;
