@@ -57,6 +57,12 @@ def parse():
     ap.add_argument("--lpnd-lps", type=int, default=65536, help="LPs of the --lpnd-only batch")
     ap.add_argument("--lp3d-only", action="store_true",
                     help="only solve the 65,536-LP ragged 3-D batch three times (for profiler captures)")
+    ap.add_argument("--class-only", type=int, nargs=2, default=None, metavar=("LO", "HI"),
+                    help="only solve (three times) a 2-D batch of LPs with sizes log-uniform in [LO, HI] "
+                         "(for profiler captures of one size class)")
+    ap.add_argument("--class-lps", type=int, default=1_000_000, help="LPs of the --class-only batch")
+    ap.add_argument("--lane-max-m", type=int, default=0,
+                    help="lane_max_m option of the --class-only solves (0: the library default, -1: none)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time only the FP32 solve (no FP64 comparator, e2e or CPU legs); for profiler captures")
     return ap.parse_args()
@@ -521,6 +527,37 @@ def run_lp3d_only(args):
                       "status_counts": np.bincount(st3.cpu().numpy(), minlength=4).tolist()}), flush=True)
 
 
+def run_class_only(args):
+    """--class-only LO HI: three solves of a 2-D batch of one size class, nothing else."""
+    import torch
+
+    from paper_1902_04995_gb300 import lp2d, workloads
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    lo, hi = args.class_only
+    sizes = workloads.loguniform_sizes(np.random.default_rng(args.seed), args.class_lps, lo, hi)
+    batch = workloads.disk_batch(sizes, seed=args.seed, infeasible_frac=0.1)
+    t = {k: torch.from_numpy(np.ascontiguousarray(batch[k]).reshape(-1)).to(dev)
+         for k in ("ax", "ay", "b", "offsets", "obj")}
+    n = len(batch["offsets"]) - 1
+    opts = lp2d.default_options(seed=args.seed, lane_max_m=args.lane_max_m)
+    ws = lp2d.new_workspace(n, opts, device=dev)
+    xy = torch.empty(2 * n, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    lp2d.solve_batch_ex(t["ax"], t["ay"], t["b"], t["offsets"], t["obj"], batch["box"], xy, st, opts, ws)
+    e0.record()
+    for _ in range(2):
+        lp2d.solve_batch_ex(t["ax"], t["ay"], t["b"], t["offsets"], t["obj"], batch["box"], xy, st, opts, ws)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"class_only": [lo, hi], "lane_max_m": args.lane_max_m, "n_lp": n,
+                      "n_constraints": int(batch["offsets"][-1]), "ms_per_solve": e0.elapsed_time(e1) / 2,
+                      "status_counts": np.bincount(st.cpu().numpy(), minlength=4).tolist()}), flush=True)
+
+
 def run_lpnd_only(args):
     """--lpnd-only D: three solves of a d-dimensional ragged batch, nothing else."""
     import torch
@@ -903,6 +940,8 @@ def main():
         run_reference(args)
     elif args.lpnd_only:
         run_lpnd_only(args)
+    elif args.class_only:
+        run_class_only(args)
     elif args.lp3d_only:
         run_lp3d_only(args)
     else:
