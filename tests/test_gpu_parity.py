@@ -352,6 +352,28 @@ def test_bad_input_and_bad_offsets():
     assert lp2d.read_device_error(ws) == 0  # reading clears it
 
 
+@pytest.mark.parametrize("lane_max_m", [-1, 16])
+def test_non_finite_objective_and_empty_lps_in_every_class(lane_max_m):
+    # a NaN or infinite objective gives BAD_INPUT whatever the LP's size class (one
+    # thread, one warp, half a CTA, a CTA); empty LPs end at the box corner
+    sizes = np.array([0, 1, 5, 16, 17, 40, 512, 700, 1500, 2049, 0, 5, 40, 700, 1500], np.int64)
+    batch = workloads.disk_batch(sizes, seed=12)
+    batch["obj"] = batch["obj"].copy()
+    batch["obj"][[2, 5, 7, 8]] = [[np.nan, 1.0], [1.0, np.inf], [-np.inf, 0.0], [np.nan, np.nan]]
+    got = gpu_solve(batch, seed=3, lane_max_m=lane_max_m)
+    ref = oracle_solve(batch, seed=3)
+    assert list(ref["status"][[2, 5, 7, 8]]) == [oracle.BAD_INPUT] * 4
+    assert (got["status"] == ref["status"]).all()
+    assert np.isnan(got["xy"][[2, 5, 7, 8]]).all()
+    assert list(ref["status"][[0, 10]]) == [oracle.BOX_BOUNDED] * 2
+    ok = ref["status"] != oracle.BAD_INPUT
+    c = np.asarray(batch["obj"], np.float64)[ok]
+    f_got = np.einsum("ij,ij->i", got["xy"][ok], c)
+    f_ref = np.einsum("ij,ij->i", ref["xy"][ok], c)
+    solved = (ref["status"][ok] == oracle.OPTIMAL) | (ref["status"][ok] == oracle.BOX_BOUNDED)
+    assert (np.abs(f_got - f_ref)[solved] <= TOL[lp2d.PREC_FP32] * np.maximum(np.abs(f_ref[solved]), 1.0)).all()
+
+
 def test_short_form_entry_point():
     batch = workloads.plain_small(seed=77)
     t = to_dev(batch)
