@@ -908,7 +908,11 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "frac_of_nominal_8000_gbs": achieved / 8000.0,
                      "peak_kind": f"{peak_kind} copy bandwidth", "traffic": profiled_traffic(WORKLOAD),
-                     "kernel": KERNEL},
+                     "kernel": KERNEL,
+                     # the ceiling that binds this kernel: instruction issue (its warp-
+                     # instructions per solve from the ncu summary of the current source)
+                     "issue": {k: v for k, v in issue_roofline(WORKLOAD, KERNEL_SOURCES, ms_max, sm_count(dev),
+                                                                None).items() if k != "hbm"}},
         "fp64_plain": {"value": n_lp / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
                        "achieved_gbs": algo_bytes / (ms64 * 1e-3) / 1e9,
                        "frac": algo_bytes / (ms64 * 1e-3) / 1e9 / peak, "status_agreement_with_fp32": status_agree,
