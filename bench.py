@@ -61,6 +61,11 @@ def parse():
                     help="only solve (three times) a 2-D batch of LPs with sizes log-uniform in [LO, HI] "
                          "(for profiler captures of one size class)")
     ap.add_argument("--class-lps", type=int, default=1_000_000, help="LPs of the --class-only batch")
+    ap.add_argument("--workload-only", default=None, metavar="NAME",
+                    help="only solve (three times) a named 2-D workload, e.g. plain_65536x256 or collision_16384 "
+                         "(for profiler captures of one config)")
+    ap.add_argument("--precision", type=int, default=0,
+                    help="precision mode of the --workload-only solves (0 FP32, 1 FP32 + FP64 intersections, 2 FP64)")
     ap.add_argument("--lane-max-m", type=int, default=0,
                     help="lane_max_m option of the --class-only solves (0: the library default, -1: none)")
     ap.add_argument("--kernel-only", action="store_true",
@@ -527,23 +532,20 @@ def run_lp3d_only(args):
                       "status_counts": np.bincount(st3.cpu().numpy(), minlength=4).tolist()}), flush=True)
 
 
-def run_class_only(args):
-    """--class-only LO HI: three solves of a 2-D batch of one size class, nothing else."""
+def solve_three_times(batch, opts):
+    """Three solves of a 2-D batch with the given options (the first untimed); returns
+    the CUDA-event time of the last two per solve and the statuses."""
     import torch
 
-    from paper_1902_04995_gb300 import lp2d, workloads
+    from paper_1902_04995_gb300 import lp2d
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    lo, hi = args.class_only
-    sizes = workloads.loguniform_sizes(np.random.default_rng(args.seed), args.class_lps, lo, hi)
-    batch = workloads.disk_batch(sizes, seed=args.seed, infeasible_frac=0.1)
     t = {k: torch.from_numpy(np.ascontiguousarray(batch[k]).reshape(-1)).to(dev)
          for k in ("ax", "ay", "b", "offsets", "obj")}
     n = len(batch["offsets"]) - 1
-    opts = lp2d.default_options(seed=args.seed, lane_max_m=args.lane_max_m)
     ws = lp2d.new_workspace(n, opts, device=dev)
-    xy = torch.empty(2 * n, device=dev)
+    xy = torch.empty(2 * n, device=dev, dtype=torch.float64 if opts.precision == lp2d.PREC_FP64 else torch.float32)
     st = torch.empty(n, dtype=torch.int32, device=dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -553,9 +555,31 @@ def run_class_only(args):
         lp2d.solve_batch_ex(t["ax"], t["ay"], t["b"], t["offsets"], t["obj"], batch["box"], xy, st, opts, ws)
     e1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"class_only": [lo, hi], "lane_max_m": args.lane_max_m, "n_lp": n,
-                      "n_constraints": int(batch["offsets"][-1]), "ms_per_solve": e0.elapsed_time(e1) / 2,
-                      "status_counts": np.bincount(st.cpu().numpy(), minlength=4).tolist()}), flush=True)
+    return e0.elapsed_time(e1) / 2, np.bincount(st.cpu().numpy(), minlength=4).tolist()
+
+
+def run_class_only(args):
+    """--class-only LO HI: three solves of a 2-D batch of one size class, nothing else."""
+    from paper_1902_04995_gb300 import lp2d, workloads
+
+    lo, hi = args.class_only
+    sizes = workloads.loguniform_sizes(np.random.default_rng(args.seed), args.class_lps, lo, hi)
+    batch = workloads.disk_batch(sizes, seed=args.seed, infeasible_frac=0.1)
+    ms, counts = solve_three_times(batch, lp2d.default_options(seed=args.seed, lane_max_m=args.lane_max_m))
+    print(json.dumps({"class_only": [lo, hi], "lane_max_m": args.lane_max_m, "n_lp": len(batch["offsets"]) - 1,
+                      "n_constraints": int(batch["offsets"][-1]), "ms_per_solve": ms, "status_counts": counts}),
+          flush=True)
+
+
+def run_workload_only(args):
+    """--workload-only NAME: three solves of a named 2-D workload, nothing else."""
+    from paper_1902_04995_gb300 import lp2d, workloads
+
+    batch = workloads.WORKLOADS[args.workload_only](seed=args.seed)
+    ms, counts = solve_three_times(batch, lp2d.default_options(seed=args.seed, precision=args.precision))
+    print(json.dumps({"workload_only": args.workload_only, "precision": args.precision,
+                      "n_lp": len(batch["offsets"]) - 1, "n_constraints": int(batch["offsets"][-1]),
+                      "ms_per_solve": ms, "status_counts": counts}), flush=True)
 
 
 def run_lpnd_only(args):
@@ -946,6 +970,8 @@ def main():
         run_lpnd_only(args)
     elif args.class_only:
         run_class_only(args)
+    elif args.workload_only:
+        run_workload_only(args)
     elif args.lp3d_only:
         run_lp3d_only(args)
     else:
