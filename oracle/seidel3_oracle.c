@@ -30,10 +30,11 @@
  *   - 1-D LPs follow the 2-D solver's rules: strict comparisons (the earliest
  *     position wins ties, box first), den == 0 excludes the line iff num < 0, the
  *     left end is taken when the objective is perpendicular to the line.
- * Parity unpinned for two of these readings: the choice of u (the axis e_j) and the
- * first-pair rule of the start decide only degenerate inputs (ties of measure zero on
- * generic data), and no pin tells them from the alternatives.  Everything else here
- * is pinned by the tests of the 3-D oracle.
+ * The first-pair rule of the start, the orientation of the frame (w = a x u) and the
+ * endpoint taken when the objective is orthogonal to the line decide which optimal
+ * point a degenerate LP returns; hand-solved LPs pin each of them.  The axis e_j
+ * itself changes no exact result (the direction of a line of the plane in R^3,
+ * -(g.w) u + (g.u) w, does not depend on it), only rounding.
  */
 #include <math.h>
 #include <stdint.h>

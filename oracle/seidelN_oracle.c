@@ -34,10 +34,9 @@
  *   - 1-D LPs on p + s E_0: strict comparisons (the earliest position wins ties, box
  *     first), a constraint with A = 0 excludes the line iff r < 0; the end at larger s
  *     is taken iff c.E_0 > 0; infeasible iff the left end exceeds the right end.
- * Parity unpinned for the tie rules of the start (the first k-subset among equally
- * good box vertices) and of the pivot (the first J among equal |A_J|): they decide
- * only degenerate inputs, and no pin tells them from the alternatives.  Everything
- * else here is pinned by the tests of the d-dimensional oracle.
+ * The tie rules of the start (the first k-subset among equally good box vertices) and
+ * of the pivot (the first J among equal |A_J|) and the endpoint rule decide which
+ * optimal point a degenerate LP returns; hand-solved LPs pin each of them.
  */
 #include <math.h>
 #include <stdint.h>

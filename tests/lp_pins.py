@@ -35,6 +35,48 @@ def load_hand_lps(path=os.path.join(GOLDEN, "hand_lps.txt")):
     return cases
 
 
+def load_hand_lps_nd(path=os.path.join(GOLDEN, "hand_lps_nd.txt")):
+    """Parse the hand-solved degenerate 3-D and d-dimensional LP fixtures."""
+    cases, cur = [], None
+    with open(path) as f:
+        for raw in f:
+            line = raw.split("#", 1)[0].strip()
+            if not line:
+                continue
+            tok = line.split()
+            if tok[0] == "lp":
+                cur = {"name": tok[1], "cons": [], "order": None}
+                cases.append(cur)
+            elif tok[0] == "solver":
+                cur["solver"] = tok[1]
+            elif tok[0] == "box":
+                cur["box"] = tuple(float(v) for v in tok[1:])
+            elif tok[0] == "obj":
+                cur["obj"] = tuple(float(v) for v in tok[1:])
+            elif tok[0] == "c":
+                cur["cons"].append(tuple(float(v) for v in tok[1:]))
+            elif tok[0] == "order":
+                cur["order"] = [int(v) for v in tok[1:]]
+            elif tok[0] == "expect":
+                cur["status"] = STATUS[tok[1]]
+                vals = [float(v) for v in tok[2:]]
+                cur["x"], cur["f"] = tuple(vals[:-1]), vals[-1]
+    for case in cases:
+        d = len(case["obj"])
+        assert len(case["box"]) == 2 * d and all(len(c) == d + 1 for c in case["cons"]), case["name"]
+        assert case["order"] is None or sorted(case["order"]) == list(range(len(case["cons"]))), case["name"]
+    return cases
+
+
+def seed_for_order(perm_array, order, tries=4096):
+    """A seed whose visit order of len(order) constraints is `order` (perm_array(seed,
+    m) lists the constraint visited at each position)."""
+    for seed in range(tries):
+        if list(perm_array(seed, len(order))) == list(order):
+            return seed
+    raise AssertionError(f"no seed below {tries} gives the visit order {order}")
+
+
 def box_rows(box):
     """Box sides as (ax, ay, b) rows with ids -1..-4 (x<=xmax, x>=xmin, y<=ymax, y>=ymin)."""
     xmin, xmax, ymin, ymax = box

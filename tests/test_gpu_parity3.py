@@ -267,3 +267,24 @@ def test_lps_beyond_the_warp_stage(prec):
     assert_parity3(batch, got, ref, TOL[prec])
     if want:
         assert (got["nviol"] == ref["nviol"]).all()
+
+
+@pytest.mark.parametrize("prec", [lp2d.PREC_FP32, lp2d.PREC_FP64])
+def test_hand_solved_degenerate_golden(prec):
+    # LPs whose optimum is not a point: the point returned is decided by the frame's
+    # orientation (R17), the start's tie rule (R18) and the endpoint rule, and must be
+    # the hand-derived one, in both visit orders where the case names one
+    import lp_pins
+
+    for case in lp_pins.load_hand_lps_nd():
+        if case["solver"] != "3d":
+            continue
+        seed = 0 if case["order"] is None else lp_pins.seed_for_order(oracle.perm_array, case["order"])
+        cons = np.asarray(case["cons"], np.float32)
+        batch = {"ax": cons[:, 0].copy(), "ay": cons[:, 1].copy(), "az": cons[:, 2].copy(), "b": cons[:, 3].copy(),
+                 "offsets": np.array([0, len(cons)], np.int64), "obj": np.asarray([case["obj"]], np.float32),
+                 "box": case["box"]}
+        got = gpu_solve3(batch, seed=seed, precision=prec)
+        assert got["status"][0] == case["status"], case["name"]
+        tol = 1e-12 if prec == lp2d.PREC_FP64 else 1e-6
+        assert np.allclose(got["xyz"][0], case["x"], rtol=0, atol=tol), (case["name"], got["xyz"][0])

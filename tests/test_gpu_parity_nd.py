@@ -266,3 +266,25 @@ def test_lps_beyond_the_warp_stage(d, prec):
     assert_parity(batch["obj"], got, ref, TOL[prec])
     if want:
         assert (got["nviol"] == ref["nviol"]).all()
+
+
+@pytest.mark.parametrize("prec", [lp2d.PREC_FP32, lp2d.PREC_FP64])
+def test_hand_solved_degenerate_golden(prec):
+    # LPs whose optimum is not a point: the point returned is decided by the pivot's and
+    # the start's tie rules (R23, R24) and the endpoint rule, and must be the
+    # hand-derived one, in both visit orders where the case names one
+    import lp_pins
+
+    for case in lp_pins.load_hand_lps_nd():
+        if case["solver"] != "nd":
+            continue
+        seed = 0 if case["order"] is None else lp_pins.seed_for_order(oracle.perm_array, case["order"])
+        d = len(case["obj"])
+        cons = np.asarray(case["cons"], np.float32)
+        batch = {"a": np.ascontiguousarray(cons[:, :d].T), "b": cons[:, d].copy(),
+                 "offsets": np.array([0, len(cons)], np.int64), "obj": np.asarray([case["obj"]], np.float32),
+                 "box": case["box"]}
+        got = gpu_solve_nd(batch, seed=seed, precision=prec)
+        assert got["status"][0] == case["status"], case["name"]
+        tol = 1e-12 if prec == lp2d.PREC_FP64 else 1e-6
+        assert np.allclose(got["x"][0], case["x"], rtol=0, atol=tol), (case["name"], got["x"][0])

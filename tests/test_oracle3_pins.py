@@ -11,6 +11,7 @@ import math
 import numpy as np
 import pytest
 
+import lp_pins
 import oracle
 from paper_1902_04995_gb300 import workloads
 
@@ -199,3 +200,24 @@ def test_least_violation_closed_form_and_highs():
         assert r["xyz"][l][2] > 1e-3  # infeasible: some violation is unavoidable
         checked += 1
     assert checked == 40
+
+
+HAND_3D = [case for case in lp_pins.load_hand_lps_nd() if case["solver"] == "3d"]
+
+
+@pytest.mark.parametrize("case", HAND_3D, ids=[case["name"] for case in HAND_3D])
+def test_hand_solved_degenerate_golden(case):
+    # readings R17 (the frame's orientation), R18 (the start's tie rule) and the
+    # endpoint rule on a line the objective is orthogonal to, pinned by LPs whose
+    # optimum is not a point: the hand-derived optimal point must come back exactly
+    seed = 0 if case["order"] is None else lp_pins.seed_for_order(oracle.perm_array, case["order"])
+    cons = np.asarray(case["cons"], np.float64)
+    r = single(cons[:, :3], cons[:, 3], case["obj"], box=case["box"], seed=seed)
+    assert r["status"][0] == case["status"], case["name"]
+    assert np.allclose(r["xyz"][0], case["x"], rtol=0, atol=1e-12), (case["name"], r["xyz"][0])
+    assert abs(float(np.dot(r["xyz"][0], case["obj"])) - case["f"]) <= 1e-12
+
+
+def test_every_hand_solved_degenerate_golden():
+    for case in HAND_3D:
+        test_hand_solved_degenerate_golden(case)

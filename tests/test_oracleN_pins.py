@@ -12,6 +12,7 @@ import math
 import numpy as np
 import pytest
 
+import lp_pins
 import oracle
 from paper_1902_04995_gb300 import workloads
 
@@ -246,3 +247,24 @@ def test_bad_input_and_zero_normals():
     r = single([[0, 0, 0, 0], [1, 1, 0, 0]], [1.0, 0.5], [1, 1, 1, 1], box)
     assert r["status"][0] == oracle.BOX_BOUNDED
     assert r["x"][0] @ np.ones(4) == pytest.approx(2.5, rel=1e-12)
+
+
+HAND_ND = [case for case in lp_pins.load_hand_lps_nd() if case["solver"] == "nd"]
+
+
+@pytest.mark.parametrize("case", HAND_ND, ids=[case["name"] for case in HAND_ND])
+def test_hand_solved_degenerate_golden(case):
+    # the tie rules of R23 (the pivot) and R24 (the start) and the endpoint rule on a
+    # line the objective is orthogonal to, pinned by LPs whose optimum is not a point
+    seed = 0 if case["order"] is None else lp_pins.seed_for_order(oracle.perm_array, case["order"])
+    cons = np.asarray(case["cons"], np.float64)
+    d = len(case["obj"])
+    r = single(cons[:, :d], cons[:, d], case["obj"], case["box"], seed=seed)
+    assert r["status"][0] == case["status"], case["name"]
+    assert np.allclose(r["x"][0], case["x"], rtol=0, atol=1e-12), (case["name"], r["x"][0])
+    assert abs(float(np.dot(r["x"][0], case["obj"])) - case["f"]) <= 1e-12
+
+
+def test_every_hand_solved_degenerate_golden():
+    for case in HAND_ND:
+        test_hand_solved_degenerate_golden(case)

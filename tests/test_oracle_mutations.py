@@ -32,11 +32,12 @@ DETECT_2D = [
     lambda: pins2.test_duplicate_pair_reports_the_earlier_visited_copy(oracle),
 ]
 DETECT_3D = [pins3.test_brute_force_on_tiny_lps, pins3.test_cube_and_box_closed_forms,
-             pins3.test_octahedron_closed_form]
+             pins3.test_octahedron_closed_form, pins3.test_every_hand_solved_degenerate_golden]
 DETECT_ND = [
     lambda: pinsN.test_brute_force_on_tiny_lps(4, 500),
     lambda: pinsN.test_hypercube_cross_polytope_and_simplex_closed_forms(4),
     lambda: pinsN.test_kkt_certificates_on_a_generated_batch(4),
+    pinsN.test_every_hand_solved_degenerate_golden,
 ]
 
 # (name, file, text, replacement, detectors)
@@ -65,6 +66,17 @@ MUTATIONS = [
      "for (int64_t f = -6; f < j - 1; f++) {", DETECT_3D),
     ("3d_wrong_start_corner", "seidel3_oracle.c", "x[k] = (c[k] >= 0.0) ? box[2 * k + 1] : box[2 * k];",
      "x[k] = (c[k] >= 0.0) ? box[2 * k] : box[2 * k + 1];", DETECT_3D),
+    ("3d_start_tie_last_pair_r18", "seidel3_oracle.c", "if (!found || val > best) {",
+     "if (!found || val >= best) {", DETECT_3D),
+    ("3d_frame_mirrored_r17", "seidel3_oracle.c", "cross3(h, F->u, F->w);", "cross3(F->u, h, F->w);", DETECT_3D),
+    ("3d_endpoint_reading_r2", "seidel3_oracle.c", "if (cd > 0.0) { tau = hi; e = id_hi; }",
+     "if (cd >= 0.0) { tau = hi; e = id_hi; }", DETECT_3D),
+    ("nd_start_tie_last_subset_r24", "seidelN_oracle.c", "if (!found || val > best) {",
+     "if (!found || val >= best) {", DETECT_ND),
+    ("nd_pivot_last_on_ties_r23", "seidelN_oracle.c", "if (fabs(A[i]) > fabs(A[J])) J = i;",
+     "if (fabs(A[i]) >= fabs(A[J])) J = i;", DETECT_ND),
+    ("nd_endpoint_reading_r2", "seidelN_oracle.c", "double s[DMAX] = {ce > 0.0 ? hi : lo};",
+     "double s[DMAX] = {ce >= 0.0 ? hi : lo};", DETECT_ND),
     ("nd_objective_end", "seidelN_oracle.c", "double s[DMAX] = {ce > 0.0 ? hi : lo};",
      "double s[DMAX] = {ce < 0.0 ? hi : lo};", DETECT_ND),
     ("nd_frame_point_sign", "seidelN_oracle.c", "T.p[t] = S->p[t] + (r / A[J]) * S->E[J][t];",
