@@ -187,7 +187,7 @@ __device__ __forceinline__ bool box_start(WT& W) {
     bool found = false;
     Real best = Real(0);
     unsigned best_mask = 0u;
-    int best_sg = 0;
+    int best_sg = 0, best_lex = 0;
 #pragma unroll 1
     for (int q0 = 0; q0 < kCands; q0 += 32) {
         const int q = q0 + W.lane;
@@ -195,6 +195,7 @@ __device__ __forceinline__ bool box_start(WT& W) {
         Real val = Real(0), xc[D];
         unsigned mask = 0u;
         const int sg = q & ((1 << K) - 1);
+        int lex = 0;  // the candidate's box planes 2a + side, in increasing order, as digits base 2D
 #pragma unroll
         for (int t = 0; t < D; ++t) xc[t] = Real(0);
         if (q < kCands) {
@@ -205,6 +206,7 @@ __device__ __forceinline__ bool box_start(WT& W) {
             for (int r = 0; r < K; ++r) {
                 const int a = __ffs(mk) - 1;
                 mk &= mk - 1u;
+                lex = lex * (2 * D) + 2 * a + ((sg >> r) & 1);
                 const Real v = ((sg >> r) & 1) ? -Real(sb[2 * a + 1]) : Real(sb[2 * a]);
                 R[r] = v - F[a];
 #pragma unroll
@@ -227,12 +229,16 @@ __device__ __forceinline__ bool box_start(WT& W) {
                 }
             }
         }
-        typename KT::type key = ok ? KT::key(val) : KT::key(-real_inf<Real>());
-        int who = ok ? W.lane : kNoPos;
-        warp_max_pair(key, who);  // the largest value, the first candidate on ties
+        // the largest value; on ties the candidate whose box planes come first in
+        // lexicographic order (R24), as the oracle enumerates them
+        const typename KT::type key = ok ? KT::key(val) : KT::key(-real_inf<Real>());
+        const typename KT::type kmax = warp_max_key(key);
+        const int lmin = __reduce_min_sync(kFull, (ok && key == kmax) ? lex : INT_MAX);
+        const unsigned hit = __ballot_sync(kFull, ok && key == kmax && lex == lmin);
+        const int who = hit != 0u ? __ffs(hit) - 1 : kNoPos;
         if (who != kNoPos) {
-            const Real v = KT::val(key);
-            const bool better = !found || v > best;
+            const Real v = KT::val(kmax);
+            const bool better = !found || v > best || (v == best && lmin < best_lex);
             found = true;
 #pragma unroll
             for (int t = 0; t < D; ++t) {
@@ -243,6 +249,7 @@ __device__ __forceinline__ bool box_start(WT& W) {
             const int bs = __shfl_sync(kFull, sg, who);
             best_mask = better ? bm : best_mask;
             best_sg = better ? bs : best_sg;
+            best_lex = better ? lmin : best_lex;
             best = better ? v : best;
         }
     }
