@@ -121,9 +121,10 @@ def test_fp64_violation_counts_and_defining_planes_match_the_oracle(d):
     got = gpu_solve_nd(batch, seed=5, precision=lp2d.PREC_FP64, want=True)
     ref = oracle_nd(batch, seed=5, want_def=True, want_nviol=True)
     assert_parity(batch["obj"], got, ref, TOL[lp2d.PREC_FP64])
-    assert (got["nviol"] == ref["nviol"]).mean() >= 0.995
+    # the same FP64 steps in the same order, ties included (R23, R24): the oracle's path
+    assert (got["nviol"] == ref["nviol"]).all()
     ok = ref["status"] != oracle.INFEASIBLE
-    assert (np.sort(got["def"][ok], 1) == np.sort(ref["def"][ok], 1)).all(1).mean() >= 0.995
+    assert (np.sort(got["def"][ok], 1) == np.sort(ref["def"][ok], 1)).all()
     assert (got["def"][~ok] == np.iinfo(np.int32).min).all()
 
 
