@@ -76,9 +76,10 @@ def test_fp64_violation_counts_and_defining_planes_match_the_oracle():
     got = gpu_solve3(batch, seed=5, precision=lp2d.PREC_FP64, want=True)
     ref = oracle3(batch, seed=5, want_def=True, want_nviol=True)
     assert_parity3(batch, got, ref, TOL[lp2d.PREC_FP64])
-    assert (got["nviol"] == ref["nviol"]).mean() >= 0.999
+    # the same FP64 steps in the same order, ties included (R17, R18): the oracle's path
+    assert (got["nviol"] == ref["nviol"]).all()
     ok = ref["status"] != oracle.INFEASIBLE
-    assert (np.sort(got["def"][ok], 1) == np.sort(ref["def"][ok], 1)).all(1).mean() >= 0.999
+    assert (np.sort(got["def"][ok], 1) == np.sort(ref["def"][ok], 1)).all()
 
 
 def test_plain3d_at_scale():
@@ -95,7 +96,6 @@ def test_ragged3d_at_scale():
 
 
 def test_edge_cases_empty_tiny_bad_and_too_large():
-    rng = np.random.default_rng(9)
     # the class boundaries (quarter and half stage), the large-LP kernel (1019 and up)
     # and its cap (12282), and one LP above it
     sizes = np.array([0, 1, 2, 3, 6, 31, 32, 33, 505, 506, 507, 1018, 1019, 2000, 5000, 12282, 12283])
@@ -105,7 +105,6 @@ def test_edge_cases_empty_tiny_bad_and_too_large():
     keep = sizes <= lp2d.MAX_CONSTRAINTS_3D
     assert (got["status"][~keep] == oracle.BAD_INPUT).all()
     assert got["err"] & lp2d.DEVERR_TOO_LARGE
-    sub = {k: v for k, v in ref.items()}
     bad = np.nonzero(got["status"][keep] != ref["status"][keep])[0]
     assert bad.size == 0, bad
     c = batch["obj"].astype(np.float64)
@@ -121,7 +120,6 @@ def test_edge_cases_empty_tiny_bad_and_too_large():
     b2["offsets"] = np.array([0, 10, 5, 30], np.int64)
     got = gpu_solve3(b2)
     assert got["status"][1] == oracle.BAD_INPUT and got["err"] & lp2d.DEVERR_BAD_OFFSETS
-    del sub, rng
 
 
 def test_results_identical_across_tuning_and_repeated_launches():
